@@ -1,0 +1,187 @@
+/*
+ * fcs.h -- C ABI of libfcs: Fast Count Sketch (FCS) on one GB300 (sm_103a).
+ *
+ * Method: X. Cao and J. Liu, "Efficient Tensor Contraction via Fast Count
+ * Sketch" (arXiv 2106.13062).  Section, definition and equation names below
+ * are the paper's.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status (FCS_OK on success).  On failure
+ *    nothing is launched (argument errors) or the CUDA error is recorded
+ *    (FCS_ECUDA); fcs_last_error() returns a message for the context.  No C++
+ *    exception crosses this boundary.
+ *  - Pointers are DEVICE pointers owned by the caller unless the parameter
+ *    name starts with `host_`.  Results are written asynchronously on the
+ *    context's stream and are valid once that stream has been synchronised.
+ *  - Indices are 0-based.  The paper's 1-based bin sum_n h_n(i_n) - N + 1 is
+ *    the bin sum_n h_n(i_n) here, so bins run over [0, Jt), with
+ *    Jt = sum_n J_n - N + 1 (Def. 4).
+ *  - Hash tables: h is int32, s is int8 (values +1/-1), both laid out
+ *    [D][ldh] with mode n of sketch d at h[d*ldh + sum_{m<n} I_m + i].
+ *    ldh = 0 means ldh = sum_n I_n (dense packing, as fcs_make_hashes writes).
+ *    A larger ldh lets a call use a contiguous run of modes of a wider table
+ *    (e.g. modes 3..4 of an order-4 table for the Kronecker workload).
+ *  - Limits: 1 <= N <= 8, 1 <= D <= 16, 1 <= J_n, I_n >= 1, every entry of
+ *    h for mode n in [0, J_n).  FFT-based calls need Jt <= 16384
+ *    (FFT length P = smallest power of two >= Jt, 16 <= P <= 16384);
+ *    larger problems return FCS_EUNSUPPORTED.
+ *  - The library allocates only its own context workspace (device memory
+ *    reused across calls, bounded by the context's budget) and a 256 KiB
+ *    twiddle table.  A context must be used from one host thread at a time.
+ *  - Floating point is FP32 throughout; sums use atomics, so the last bits
+ *    of a result may differ from run to run.  Hashes and bins are exact.
+ */
+#ifndef FCS_H
+#define FCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FCS_OK 0
+#define FCS_EINVAL 1          /* bad argument (shape, pointer, limit)        */
+#define FCS_ENOMEM_BUDGET 2   /* workspace would exceed the context budget    */
+#define FCS_ECUDA 3           /* a CUDA runtime call failed                   */
+#define FCS_ETIMEOUT 4        /* a bounded device wait gave up                */
+#define FCS_EUNSUPPORTED 5    /* valid but outside what this build supports  */
+
+/* contraction kinds for fcs_contract */
+#define FCS_CONTRACT_ALL 0    /* T(v_1, ..., v_N): one scalar per batch item  */
+#define FCS_CONTRACT_FREE 1   /* T(v_1, .., I (mode m), .., v_N): a vector    */
+
+typedef struct fcs_ctx fcs_ctx;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int fcs_version(void);
+
+/* Create a context on CUDA device `device`, issuing all work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  `mem_budget_bytes`
+ * caps the workspace the context may hold; (size_t)-1 means no cap, 0 means
+ * no workspace at all (calls that need one return FCS_ENOMEM_BUDGET).
+ * Allocates the twiddle table (exp(-2 pi i k / 32768), k < 32768, computed in
+ * FP64 on the device and rounded to FP32).  *ctx is NULL on failure. */
+int fcs_create(fcs_ctx **ctx, int device, void *stream, size_t mem_budget_bytes);
+
+/* Release the context, its workspace and twiddle table (synchronises its
+ * stream first).  NULL is accepted. */
+int fcs_destroy(fcs_ctx *ctx);
+
+/* Change the stream later calls are issued on. */
+int fcs_set_stream(fcs_ctx *ctx, void *stream);
+
+/* Message for the last failing call on this context ("" if none).  The
+ * pointer stays valid until the next call on the context. */
+const char *fcs_last_error(const fcs_ctx *ctx);
+
+/* Bytes of device workspace the context holds now. */
+size_t fcs_workspace_bytes(const fcs_ctx *ctx);
+
+/*
+ * fcs_make_hashes -- the N hash pairs {h_n, s_n} of Def. 4 for D independent
+ * sketches (the paper asks for 2-wise independent pairs, Def. 1; it fixes no
+ * family).  Family: Carter-Wegman multiply-mod-prime over p = 2^61 - 1,
+ *     h_n(i) = ((a_h i + b_h) mod p) mod J_n,
+ *     s_n(i) = 1 - 2 (((a_s i + b_s) mod p) & 1),
+ * with a = 1 + x mod (p-1), b = x mod p drawn from SplitMix64 seeded with
+ * `seed`, four draws (a_h, b_h, a_s, b_s) per (d, n) in the order d-major,
+ * n-minor.  Deterministic in (seed, N, I, J, D) and bit-identical to the
+ * CPU oracle.
+ *   host_I[N], host_J[N]: mode sizes and hash lengths (host memory).
+ *   h [D][sum I] int32, s [D][sum I] int8: outputs, densely packed.
+ */
+int fcs_make_hashes(fcs_ctx *ctx, uint64_t seed, int N, const int64_t *host_I,
+                    const int32_t *host_J, int D, int32_t *h, int8_t *s);
+
+/*
+ * fcs_sketch_dense -- FCS of a general tensor by the signed scatter of
+ * eq. (FCS_asyn):  out_d[sum_n h_n(i_n)] += prod_n s_n(i_n) T(i_1..i_N).
+ *   host_I[N]: mode sizes; host_stride[N]: element strides of T (NULL = C
+ *   order, last mode contiguous); T: FP32 tensor; out [D][Jt] FP32 (zeroed
+ *   by the call, then accumulated).  nbatch tensors of the same shape may be
+ *   sketched in one launch: tensor b starts at T + b*T_batch_stride and its
+ *   sketch at out + b*out_batch_stride (elements; nbatch = 1 ignores both).
+ */
+int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
+                     const int64_t *host_stride, const int32_t *host_J, int D,
+                     const float *T, const int32_t *h, const int8_t *s,
+                     int64_t ldh, float *out, int64_t nbatch,
+                     int64_t T_batch_stride, int64_t out_batch_stride);
+
+/*
+ * fcs_sketch_cp -- FCS of a CP tensor [[lambda; U_1..U_N]] by eq. (FCS_syn):
+ * per mode the Count Sketch of every factor column (Def. 1), a zero-padded
+ * real FFT of length P >= Jt, the mode-wise product, the lambda-weighted sum
+ * over rank (kept in the frequency domain; by linearity this equals the
+ * paper's sum of inverse transforms) and one inverse FFT per sketch.
+ *   host_U[N]: device pointers; U_n is I_n x R FP32 row-major with leading
+ *   dimension host_ldU[n] >= R.  lambda [R] FP32 or NULL (all ones).
+ *   out [D][Jt] FP32.  Needs D*(P/2+1)*8 + 64 bytes of workspace.
+ */
+int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
+                  const int32_t *host_J, int64_t R, int D,
+                  const float *const *host_U, const int64_t *host_ldU,
+                  const float *lambda, const int32_t *h, const int8_t *s,
+                  int64_t ldh, float *out);
+
+/*
+ * fcs_contract -- sketched contractions of Sec. 4.1, one per batch item b:
+ *  kind FCS_CONTRACT_ALL, eq. (T_uvw):
+ *      raw[b][d] = < FCS_d(T), FCS_d(v_1 o ... o v_N) >, evaluated as
+ *      (1/P) Re sum_k conj(F(FCS_d T))[k] prod_n F(CS_n v_n)[k] (Parseval);
+ *      out_median[b] = median_d raw[b][d].
+ *  kind FCS_CONTRACT_FREE with free mode m, eq. (T_Ivw) (m = 0) and the ALS
+ *  columns T_(m)(...) (any m):
+ *      z_d = IFFT(F(FCS_d T) prod_{n != m} conj F(CS_n v_n)),
+ *      raw[b][d][i] = s_m(i) z_d[h_m(i)],  out_median[b][i] = median_d.
+ *  fcsT [D][Jt]: the tensor's sketches (e.g. from fcs_sketch_dense).
+ *  host_vecs[N]: device pointers, vector n is [B][I_n] FP32 (row b
+ *  contiguous); for FREE the pointer of mode m is ignored and may be NULL.
+ *  out_median: [B] (ALL) or [B][I_m] (FREE).  out_raw: NULL or [B][D] (ALL)
+ *  / [B][D][I_m] (FREE).  Median over even D is the mean of the two middle
+ *  values.  Needs D*(P/2+1)*8 bytes of workspace (+ the raw buffer when
+ *  out_raw is NULL).
+ */
+int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
+                 const int64_t *host_I, const int32_t *host_J, int D,
+                 const float *fcsT, int64_t B, const float *const *host_vecs,
+                 const int32_t *h, const int8_t *s, int64_t ldh,
+                 float *out_median, float *out_raw);
+
+/*
+ * fcs_recover -- entry estimates from sketches, the decompressing rule of the
+ * Kronecker / tensor-contraction compression subsections (its mod(., Jt) never
+ * wraps and is dropped):
+ *     raw[d][q] = prod_n s_n(i_n) sketch_d[sum_n h_n(i_n)],  out[q] = median_d.
+ *   sketch [D][Jt]; idx [M][N] int32 multi-indices (i_n < I_n; not checked on
+ *   the device).  out [M]; out_raw NULL or [D][M].  nbatch problems sharing the
+ *   hash tables: problem b uses sketch + b*sketch_batch_stride, idx +
+ *   b*idx_batch_stride, out + b*out_batch_stride (elements; out_raw must be
+ *   NULL when nbatch > 1).
+ */
+int fcs_recover(fcs_ctx *ctx, int N, const int64_t *host_I,
+                const int32_t *host_J, int D, const float *sketch,
+                const int32_t *h, const int8_t *s, int64_t ldh, int64_t M,
+                const int32_t *idx, float *out, float *out_raw, int64_t nbatch,
+                int64_t sketch_batch_stride, int64_t idx_batch_stride,
+                int64_t out_batch_stride);
+
+/*
+ * fcs_sketch_outer -- sketch of an outer product (Kronecker product
+ * compression): FCS(A o B) = IFFT(FFT(FCS A) * FFT(FCS B)), zero-padded to a
+ * power of two P >= La + Lb - 1, i.e. the full linear convolution of the two
+ * sketches.  fa [nbatch][D][La], fb [nbatch][D][Lb] -> out
+ * [nbatch][D][La+Lb-1], all contiguous FP32.
+ */
+int fcs_sketch_outer(fcs_ctx *ctx, int64_t nbatch, int D, int64_t La,
+                     int64_t Lb, const float *fa, const float *fb, float *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCS_H */

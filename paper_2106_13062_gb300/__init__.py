@@ -1,0 +1,334 @@
+"""Fast Count Sketch (Cao & Liu, "Efficient Tensor Contraction via Fast Count
+Sketch") on one GB300: a thin Python binding over the C ABI of ``libfcs.so``.
+
+Every function here only marshals arguments (torch tensors -> device pointers
+and sizes, the current torch stream) and calls the C entry point of the same
+name; all arithmetic runs in the library's CUDA kernels.  There is no CPU path:
+if ``libfcs.so`` is missing or no GPU is present, calls raise.
+
+Names follow the C ABI (``include/fcs.h``):
+    fcs_make_hashes, fcs_sketch_dense, fcs_sketch_cp, fcs_contract,
+    fcs_recover, fcs_sketch_outer
+plus ``Context`` (fcs_create / fcs_destroy) and ``build()``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from .build import LIB as _LIB_PATH, build  # noqa: F401
+
+FCS_OK = 0
+FCS_EINVAL = 1
+FCS_ENOMEM_BUDGET = 2
+FCS_ECUDA = 3
+FCS_ETIMEOUT = 4
+FCS_EUNSUPPORTED = 5
+FCS_CONTRACT_ALL = 0
+FCS_CONTRACT_FREE = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FcsError(RuntimeError):
+    """A libfcs call returned a non-zero status."""
+
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libfcs status {code}: {msg}")
+        self.code = code
+
+
+def lib() -> C.CDLL:
+    """Load libfcs.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(
+                    f"{_LIB_PATH} is missing: build it with "
+                    "paper_2106_13062_gb300.build() (nvcc, sm_103a)")
+            L = C.CDLL(_LIB_PATH)
+            vp, i64p, i32p, i8p, f32p = (C.c_void_p, C.POINTER(C.c_int64),
+                                         C.POINTER(C.c_int32), C.c_void_p,
+                                         C.c_void_p)
+            sig = {
+                "fcs_version": (C.c_int, []),
+                "fcs_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, vp,
+                                         C.c_size_t]),
+                "fcs_destroy": (C.c_int, [vp]),
+                "fcs_set_stream": (C.c_int, [vp, vp]),
+                "fcs_last_error": (C.c_char_p, [vp]),
+                "fcs_workspace_bytes": (C.c_size_t, [vp]),
+                "fcs_make_hashes": (C.c_int, [vp, C.c_uint64, C.c_int, i64p, i32p,
+                                              C.c_int, vp, vp]),
+                "fcs_sketch_dense": (C.c_int, [vp, C.c_int, i64p, i64p, i32p,
+                                               C.c_int, vp, vp, vp, C.c_int64,
+                                               vp, C.c_int64, C.c_int64,
+                                               C.c_int64]),
+                "fcs_sketch_cp": (C.c_int, [vp, C.c_int, i64p, i32p, C.c_int64,
+                                            C.c_int, C.POINTER(C.c_void_p), i64p,
+                                            vp, vp, vp, C.c_int64, vp]),
+                "fcs_contract": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, i64p,
+                                           i32p, C.c_int, vp, C.c_int64,
+                                           C.POINTER(C.c_void_p), vp, vp,
+                                           C.c_int64, vp, vp]),
+                "fcs_recover": (C.c_int, [vp, C.c_int, i64p, i32p, C.c_int, vp,
+                                          vp, vp, C.c_int64, C.c_int64, vp, vp,
+                                          vp, C.c_int64, C.c_int64, C.c_int64,
+                                          C.c_int64]),
+                "fcs_sketch_outer": (C.c_int, [vp, C.c_int64, C.c_int, C.c_int64,
+                                               C.c_int64, vp, vp, vp]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            del i8p, f32p
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects libfcs.so to export."""
+    return ["fcs_version", "fcs_create", "fcs_destroy", "fcs_set_stream",
+            "fcs_last_error", "fcs_workspace_bytes", "fcs_make_hashes",
+            "fcs_sketch_dense", "fcs_sketch_cp", "fcs_contract", "fcs_recover",
+            "fcs_sketch_outer"]
+
+
+# ------------------------------------------------------------------ helpers
+def _arr(ctype, vals):
+    vals = [int(v) for v in vals]
+    return (ctype * max(1, len(vals)))(*vals)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _need(t: torch.Tensor, dtype, name: str, contiguous: bool = True):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if contiguous and not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def jtilde(J) -> int:
+    """Sketch length of Def. 4: sum_n J_n - N + 1."""
+    return int(sum(int(j) for j in J) - len(J) + 1)
+
+
+class Context:
+    """An fcs_ctx bound to one device and (by default) torch's current
+    stream of that device at each call."""
+
+    def __init__(self, device: int | None = None, budget: int | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libfcs needs a CUDA GPU; none is available")
+        self.device = torch.cuda.current_device() if device is None else device
+        h = C.c_void_p()
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        b = C.c_size_t(-1).value if budget is None else int(budget)
+        rc = lib().fcs_create(C.byref(h), self.device, C.c_void_p(stream), b)
+        if rc != FCS_OK:
+            raise FcsError(rc, "fcs_create failed")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _sync_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        lib().fcs_set_stream(self._h, C.c_void_p(s))
+
+    def check(self, rc: int):
+        if rc != FCS_OK:
+            msg = lib().fcs_last_error(self._h).decode(errors="replace")
+            raise FcsError(rc, msg)
+
+    def workspace_bytes(self) -> int:
+        return int(lib().fcs_workspace_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().fcs_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ calls
+def fcs_make_hashes(ctx: Context, seed: int, I, J, D: int):
+    """Hash/sign tables of Def. 4 for D sketches: (h int32 [D, sum I],
+    s int8 [D, sum I]) on ctx's device."""
+    ctx._sync_stream()
+    tot = int(sum(int(i) for i in I))
+    dev = torch.device("cuda", ctx.device)
+    h = torch.empty((D, tot), dtype=torch.int32, device=dev)
+    s = torch.empty((D, tot), dtype=torch.int8, device=dev)
+    ctx.check(lib().fcs_make_hashes(ctx.handle, C.c_uint64(int(seed)), len(I),
+                                    _arr(C.c_int64, I), _arr(C.c_int32, J), D,
+                                    _ptr(h), _ptr(s)))
+    return h, s
+
+
+def fcs_sketch_dense(ctx: Context, T: torch.Tensor, J, h, s, ldh: int = 0,
+                     batched: bool = False, out: torch.Tensor | None = None):
+    """Eq. (FCS_asyn) dense-route FCS of T (any element strides).  With
+    batched=True the first dimension of T indexes independent tensors.
+    Returns [D, Jt] (or [B, D, Jt])."""
+    ctx._sync_stream()
+    _need(T, torch.float32, "T", contiguous=False)
+    _need(h, torch.int32, "h")
+    _need(s, torch.int8, "s")
+    D = h.shape[0]
+    Jt = jtilde(J)
+    shape = list(T.shape[1:] if batched else T.shape)
+    strides = list(T.stride()[1:] if batched else T.stride())
+    nb = T.shape[0] if batched else 1
+    if len(shape) != len(J):
+        raise ValueError("T's order does not match len(J)")
+    if out is None:
+        out = torch.empty(((nb,) if batched else ()) + (D, Jt),
+                          dtype=torch.float32, device=T.device)
+    _need(out, torch.float32, "out")
+    ctx.check(lib().fcs_sketch_dense(
+        ctx.handle, len(J), _arr(C.c_int64, shape), _arr(C.c_int64, strides),
+        _arr(C.c_int32, J), D, _ptr(T), _ptr(h), _ptr(s), ldh, _ptr(out), nb,
+        T.stride(0) if batched else 0, D * Jt))
+    return out
+
+
+def fcs_sketch_cp(ctx: Context, U, lam, J, h, s, ldh: int = 0,
+                  out: torch.Tensor | None = None):
+    """Eq. (FCS_syn) CP-route FCS of [[lam; U_1..U_N]] (U_n: I_n x R FP32,
+    row-major).  Returns [D, Jt]."""
+    ctx._sync_stream()
+    _need(h, torch.int32, "h")
+    _need(s, torch.int8, "s")
+    N = len(U)
+    R = U[0].shape[1]
+    for k, u in enumerate(U):
+        _need(u, torch.float32, f"U[{k}]", contiguous=False)
+        if u.dim() != 2 or u.shape[1] != R or u.stride(1) != 1:
+            raise ValueError("each U_n must be I_n x R with unit column stride")
+    if lam is not None:
+        _need(lam, torch.float32, "lambda")
+    D = h.shape[0]
+    Jt = jtilde(J)
+    if out is None:
+        out = torch.empty((D, Jt), dtype=torch.float32, device=U[0].device)
+    _need(out, torch.float32, "out")
+    ptrs = (C.c_void_p * N)(*[u.data_ptr() for u in U])
+    ctx.check(lib().fcs_sketch_cp(
+        ctx.handle, N, _arr(C.c_int64, [u.shape[0] for u in U]),
+        _arr(C.c_int32, J), R, D, ptrs, _arr(C.c_int64, [u.stride(0) for u in U]),
+        _ptr(lam), _ptr(h), _ptr(s), ldh, _ptr(out)))
+    return out
+
+
+def fcs_contract(ctx: Context, kind: int, fcsT: torch.Tensor, vecs, I, J, h, s,
+                 free_mode: int = 0, ldh: int = 0, raw: bool = False):
+    """Sketched contractions (eqs. T_uvw / T_Ivw).  vecs[n]: [B, I_n] FP32
+    (vecs[free_mode] may be None for FCS_CONTRACT_FREE).  Returns the median
+    over sketches ([B] or [B, I_m]) and, with raw=True, also the per-sketch
+    values ([B, D] or [B, D, I_m])."""
+    ctx._sync_stream()
+    _need(fcsT, torch.float32, "fcsT")
+    _need(h, torch.int32, "h")
+    _need(s, torch.int8, "s")
+    N = len(J)
+    D = fcsT.shape[0]
+    B = None
+    ptrs = (C.c_void_p * N)()
+    for n in range(N):
+        v = vecs[n]
+        if kind == FCS_CONTRACT_FREE and n == free_mode:
+            ptrs[n] = None
+            continue
+        _need(v, torch.float32, f"vecs[{n}]")
+        B = v.shape[0] if B is None else B
+        if v.shape != (B, int(I[n])):
+            raise ValueError(f"vecs[{n}] must be [B, I_{n}]")
+        ptrs[n] = v.data_ptr()
+    if B is None:
+        raise ValueError("no vectors given")
+    dev = fcsT.device
+    if kind == FCS_CONTRACT_ALL:
+        med = torch.empty((B,), dtype=torch.float32, device=dev)
+        rawt = torch.empty((B, D), dtype=torch.float32, device=dev) if raw else None
+    else:
+        Im = int(I[free_mode])
+        med = torch.empty((B, Im), dtype=torch.float32, device=dev)
+        rawt = (torch.empty((B, D, Im), dtype=torch.float32, device=dev)
+                if raw else None)
+    ctx.check(lib().fcs_contract(
+        ctx.handle, kind, free_mode, N, _arr(C.c_int64, I), _arr(C.c_int32, J), D,
+        _ptr(fcsT), B, ptrs, _ptr(h), _ptr(s), ldh, _ptr(med), _ptr(rawt)))
+    return (med, rawt) if raw else med
+
+
+def fcs_recover(ctx: Context, sketch: torch.Tensor, I, J, h, s, idx: torch.Tensor,
+                ldh: int = 0, raw: bool = False):
+    """Entry recovery (decompressing rule): median over sketches of
+    prod s * sketch[sum h].  sketch [D, Jt] with idx [M, N], or batched
+    sketch [B, D, Jt] with idx [B, M, N].  Returns [M] (or [B, M]), plus the
+    raw [D, M] values with raw=True (unbatched only)."""
+    ctx._sync_stream()
+    _need(sketch, torch.float32, "sketch")
+    _need(idx, torch.int32, "idx")
+    _need(h, torch.int32, "h")
+    _need(s, torch.int8, "s")
+    N = len(J)
+    batched = sketch.dim() == 3
+    nb = sketch.shape[0] if batched else 1
+    D = sketch.shape[-2]
+    M = idx.shape[-2]
+    if idx.shape[-1] != N:
+        raise ValueError("idx must be [.., M, N]")
+    out = torch.empty(((nb,) if batched else ()) + (M,), dtype=torch.float32,
+                      device=sketch.device)
+    rawt = None
+    if raw:
+        if batched:
+            raise ValueError("raw output is only available unbatched")
+        rawt = torch.empty((D, M), dtype=torch.float32, device=sketch.device)
+    ctx.check(lib().fcs_recover(
+        ctx.handle, N, _arr(C.c_int64, I), _arr(C.c_int32, J), D, _ptr(sketch),
+        _ptr(h), _ptr(s), ldh, M, _ptr(idx), _ptr(out), _ptr(rawt), nb,
+        D * sketch.shape[-1] if batched else 0, M * N if batched else 0,
+        M if batched else 0))
+    return (out, rawt) if raw else out
+
+
+def fcs_sketch_outer(ctx: Context, fa: torch.Tensor, fb: torch.Tensor):
+    """Sketch of an outer product from its factors' sketches (Kronecker
+    compression): full linear convolution per sketch.  fa [.., D, La],
+    fb [.., D, Lb] -> [.., D, La+Lb-1]."""
+    ctx._sync_stream()
+    _need(fa, torch.float32, "fa")
+    _need(fb, torch.float32, "fb")
+    if fa.shape[:-1] != fb.shape[:-1]:
+        raise ValueError("fa and fb must share leading dimensions")
+    D = fa.shape[-2]
+    La, Lb = fa.shape[-1], fb.shape[-1]
+    nb = fa.numel() // (D * La)
+    out = torch.empty(fa.shape[:-1] + (La + Lb - 1,), dtype=torch.float32,
+                      device=fa.device)
+    ctx.check(lib().fcs_sketch_outer(ctx.handle, nb, D, La, Lb, _ptr(fa),
+                                     _ptr(fb), _ptr(out)))
+    return out

@@ -1,0 +1,105 @@
+// fcs_outer.cu -- fcs_sketch_outer: sketch of an outer product from the
+// sketches of its factors (Kronecker product compression):
+//   FCS(A o B) = IFFT_P( FFT_P(FCS A) * FFT_P(FCS B) ),  P >= La + Lb - 1,
+// i.e. the full linear convolution of the two sketches.  One CTA per
+// (batch item, sketch): two real forward FFTs in shared memory, the product
+// kept in registers, one inverse real FFT.
+#include "fcs_internal.cuh"
+
+namespace fcs {
+namespace {
+
+template <int LOG2M, int NT>
+__global__ void __launch_bounds__(NT) outer_kernel(const float *__restrict__ fa,
+                                                   const float *__restrict__ fb, int64_t La,
+                                                   int64_t Lb, int D, float *__restrict__ out,
+                                                   const float2 *__restrict__ tw) {
+  constexpr int M = 1 << LOG2M;
+  constexpr int HALF = M / 2;
+  constexpr int EP = (HALF + NT - 1) / NT;
+  extern __shared__ __align__(16) float2 buf[];
+  float *bufr = reinterpret_cast<float *>(buf);
+  const int tid = threadIdx.x;
+  const int64_t item = int64_t(blockIdx.y) * D + blockIdx.x;   // (b, d)
+  float2 pA[EP], pB[EP];
+  for (int side = 0; side < 2; ++side) {
+    const int64_t len = side == 0 ? La : Lb;
+    const float *x = (side == 0 ? fa : fb) + item * len;
+    for (int e = tid; e < padded_len(M); e += NT) buf[e] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int64_t j = tid; j < len; j += NT) bufr[real_off(int(j))] = __ldg(x + j);
+    __syncthreads();
+    block_fft<LOG2M, NT>(buf, tw);
+#pragma unroll
+    for (int e = 0; e < EP; ++e) {
+      const int q = tid + e * NT;
+      if (q < HALF) {
+        float2 A, B;
+        unpack_pair<LOG2M>(buf, q, tw, A, B);
+        if (side == 0) {
+          pA[e] = A;
+          pB[e] = B;
+        } else {
+          pA[e] = slot_mul(pA[e], A, q == 0);
+          pB[e] = cmul(pB[e], B);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int e = 0; e < EP; ++e) {
+    const int q = tid + e * NT;
+    if (q < HALF) pack_pair_conj<LOG2M>(buf, q, pA[e], pB[e], tw);
+  }
+  __syncthreads();
+  block_fft<LOG2M, NT>(buf, tw);
+  const int64_t Lo = La + Lb - 1;
+  float *o = out + item * Lo;
+  const float sc = 1.0f / float(M);
+  for (int64_t j = tid; j < Lo; j += NT) {
+    const float v = bufr[real_off(int(j))];
+    o[j] = (j & 1) ? -v * sc : v * sc;
+  }
+}
+
+template <int LOG2M>
+int launch_outer(fcs_ctx *ctx, int64_t nbatch, int D, int64_t La, int64_t Lb,
+                 const float *fa, const float *fb, float *out) {
+  constexpr int NT = fft_threads(LOG2M);
+  const size_t smem = sizeof(float2) * padded_len(1 << LOG2M);
+  auto kern = outer_kernel<LOG2M, NT>;
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(outer)");
+  }
+  kern<<<dim3(unsigned(D), unsigned(nbatch)), NT, smem, ctx->stream>>>(fa, fb, La, Lb, D, out,
+                                                                       ctx->twiddle);
+  return check_cuda(ctx, cudaGetLastError(), "outer_kernel");
+}
+
+}  // namespace
+}  // namespace fcs
+
+using namespace fcs;
+
+extern "C" int fcs_sketch_outer(fcs_ctx *ctx, int64_t nbatch, int D, int64_t La, int64_t Lb,
+                                const float *fa, const float *fb, float *out) {
+  if (!ctx) return FCS_EINVAL;
+  ctx->err.clear();
+  if (D < 1 || D > kMaxD) return set_error(ctx, FCS_EINVAL, "D=%d outside [1,%d]", D, kMaxD);
+  if (nbatch < 1 || nbatch > 65535)
+    return set_error(ctx, FCS_EINVAL, "nbatch=%lld outside [1,65535]", (long long)nbatch);
+  if (La < 1 || Lb < 1) return set_error(ctx, FCS_EINVAL, "sketch lengths must be >= 1");
+  if (!fa || !fb || !out) return set_error(ctx, FCS_EINVAL, "NULL pointer argument");
+  const int64_t Lo = La + Lb - 1;
+  const int log2p = ilog2_ceil(Lo) < kMinLog2P ? kMinLog2P : ilog2_ceil(Lo);
+  if (log2p > kMaxLog2P)
+    return set_error(ctx, FCS_EUNSUPPORTED, "output length %lld needs FFT length > %d",
+                     (long long)Lo, 1 << kMaxLog2P);
+  DeviceGuard g(ctx->device);
+  int rc = FCS_EUNSUPPORTED;
+  FCS_DISPATCH_LOG2M(log2p - 1, rc = launch_outer<L>(ctx, nbatch, D, La, Lb, fa, fb, out));
+  return rc;
+}
