@@ -3,18 +3,22 @@
 // with P the smallest power of two >= Jt (any P >= Jt gives the exact linear
 // convolution, so out = the first Jt samples).
 //
-// One fused kernel.  CTA (g, d) owns sketch d and a contiguous group of
+// Two kernels.  (1) A transpose writes the factor columns contiguously
+// (lambda folded into mode 1) so every column load is coalesced.  (2) The
+// fused sketch kernel: CTA (g, d) owns sketch d and a contiguous group of
 // ranks.  For each rank and mode it scatters the signed factor column into a
-// zeroed shared-memory buffer (the Count Sketch of Def. 1), runs a block-wide
-// real FFT of length P (a complex FFT of length P/2 plus the pair unpack),
-// and multiplies the half spectrum into per-thread registers; after the last
-// mode it adds lambda_r times the product into a per-thread accumulator.  The
-// rank sum therefore stays in the frequency domain (linearity moves the
-// paper's sum of inverse transforms inside one inverse transform).  Each CTA
-// adds its partial spectrum into a global accumulator with atomics; the last
-// CTA to finish for sketch d (ticket counter) runs the single inverse real FFT
-// and writes FCS_d.
-#include "fcs_internal.cuh"
+// compact shared-memory buffer of max_n J_n reals (the Count Sketch of
+// Def. 1; the zero padding up to P is never stored), runs the block real FFT
+// of fcs_fft.cuh whose last pass leaves the half spectrum in registers, and
+// multiplies it into the per-thread mode product; after the last mode the
+// product is added into a shared-memory rank accumulator.  The rank sum thus
+// stays in the frequency domain (linearity moves the paper's sum of inverse
+// transforms inside one inverse transform).  Each CTA adds its partial
+// spectrum into a global accumulator with float2 atomics; the last CTA to
+// finish for sketch d (ticket counter) runs the one inverse real FFT and
+// writes FCS_d.  The next column's factor values and hashes are prefetched
+// into registers while the current column is transformed.
+#include "fcs_fft.cuh"
 
 namespace fcs {
 namespace {
@@ -24,97 +28,170 @@ struct CpArgs {
   int D;
   int64_t R;
   int64_t ranks_per_cta;
-  const float *U[kMaxN];
-  int64_t ldU[kMaxN];
-  const float *lambda;
+  const float *UT;       // [sum_n R*I_n]: mode n column r at ut_off[n] + r*I_n
+  int64_t ut_off[kMaxN];
   const int32_t *h;
   const int8_t *s;
   float2 *G;             // [D][M+1] spectrum accumulator, zeroed per call
   unsigned *counter;     // [D] tickets, zero at launch, reset by the last CTA
   float *out;            // [D][Jt]
+  int sb;                // scatter buffer length (floats): max J_n rounded up to 4
 };
 
+// UT[n][r][i] = U_n[i*ld + r] (times lambda_r for n = 0).
+__global__ void transpose_factors_kernel(const float *__restrict__ U, int64_t I, int64_t R,
+                                         int64_t ld, const float *__restrict__ lambda,
+                                         float *__restrict__ UT) {
+  __shared__ float tile[32][33];
+  const int64_t i0 = blockIdx.x * 32ll, r0 = blockIdx.y * 32ll;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t i = i0 + k, r = r0 + threadIdx.x;
+    if (i < I && r < R) tile[k][threadIdx.x] = U[i * ld + r];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + k, i = i0 + threadIdx.x;
+    if (i < I && r < R) {
+      const float lam = lambda ? __ldg(lambda + r) : 1.f;
+      UT[r * I + i] = tile[threadIdx.x][k] * lam;
+    }
+  }
+}
+
+// Shared-memory layout of cp_kernel; every region starts on a 16-byte
+// boundary (the scatter buffer is cleared with float4 stores).
 template <int LOG2M, int NT>
+struct CpSmem {
+  static constexpr size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
+  static constexpr size_t kB = 0;
+  static constexpr size_t kAcc = up16(kB + sizeof(float2) * padded_len(1 << LOG2M));
+  static constexpr size_t kTw =
+      up16(kAcc + sizeof(float2) * LastPass<LOG2M, NT>::NV * NT);
+  static constexpr size_t kA = up16(kTw + sizeof(float2) * plan_twlen(LOG2M));
+  static size_t bytes(int sb) { return kA + sizeof(float) * size_t(sb); }
+};
+
+template <int LOG2M, int NT, int CPT>
 __global__ void __launch_bounds__(NT) cp_kernel(CpArgs a, const float2 *__restrict__ tw) {
+  using LPs = LastPass<LOG2M, NT>;
   constexpr int M = 1 << LOG2M;
   constexpr int HALF = M / 2;
-  constexpr int EP = (HALF + NT - 1) / NT;
-  extern __shared__ __align__(16) float2 buf[];
-  float *bufr = reinterpret_cast<float *>(buf);
+  constexpr int RL = LPs::RL, EPS = LPs::EPS, NV = LPs::NV;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using Lay = CpSmem<LOG2M, NT>;
+  float2 *B = reinterpret_cast<float2 *>(smem_raw + Lay::kB);      // padded_len(M)
+  float2 *accS = reinterpret_cast<float2 *>(smem_raw + Lay::kAcc); // NV * NT
+  float2 *tws = reinterpret_cast<float2 *>(smem_raw + Lay::kTw);   // plan_twlen
+  float *A = reinterpret_cast<float *>(smem_raw + Lay::kA);        // a.sb floats
   __shared__ int is_last;
   const int tid = threadIdx.x;
   const int d = blockIdx.y;
+  const int N = a.m.N;
   const int64_t r0 = blockIdx.x * a.ranks_per_cta;
   const int64_t r1 = min(a.R, r0 + a.ranks_per_cta);
+  const int sb = a.sb;
 
-  float2 accA[EP], accB[EP], pA[EP], pB[EP];
+  fill_twiddles<LOG2M, NT>(tws, tw);
+  for (int e = tid; e < sb / 4; e += NT) reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-  for (int e = 0; e < EP; ++e) {
-    accA[e] = accB[e] = make_float2(0.f, 0.f);
-    pA[e] = pB[e] = make_float2(0.f, 0.f);
-  }
+  for (int v = 0; v < NV; ++v) accS[v * NT + tid] = make_float2(0.f, 0.f);
 
-  for (int64_t r = r0; r < r1; ++r) {
-    for (int n = 0; n < a.m.N; ++n) {
-      for (int e = tid; e < padded_len(M); e += NT) buf[e] = make_float2(0.f, 0.f);
-      __syncthreads();
-      const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
-      const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
-      const float *Un = a.U[n];
-      const int64_t ld = a.ldU[n];
-      for (int64_t i = tid; i < a.m.I[n]; i += NT) {
-        float v = __ldg(Un + i * ld + r);
-        if (__ldg(sn + i) < 0) v = -v;
-        const int p = __ldg(hn + i);
-        if (unsigned(p) < unsigned(2 * M)) atomicAdd(bufr + real_off(p), v);
+  // prefetched column: signed factor values and hash bins
+  float pv[CPT];
+  int ph[CPT];
+  auto fetch = [&](int64_t r, int n) {
+    const int64_t In = a.m.I[n];
+    const float *col = a.UT + a.ut_off[n] + r * In;
+    const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
+    const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int64_t i = tid + int64_t(c) * NT;
+      ph[c] = -1;
+      pv[c] = 0.f;
+      if (i < In) {
+        const float v = __ldg(col + i);
+        pv[c] = __ldg(sn + i) < 0 ? -v : v;
+        ph[c] = __ldg(hn + i);
       }
-      __syncthreads();
-      block_fft<LOG2M, NT>(buf, tw);
+    }
+  };
+  fetch(r0, 0);
+  __syncthreads();
+
+  float2 X[EPS][2][RL], p[EPS][2][RL];
+  for (int64_t r = r0; r < r1; ++r) {
+    for (int n = 0; n < N; ++n) {
 #pragma unroll
-      for (int e = 0; e < EP; ++e) {
-        const int q = tid + e * NT;
-        if (q < HALF) {
-          float2 A, B;
-          unpack_pair<LOG2M>(buf, q, tw, A, B);
-          if (n == 0) {
-            pA[e] = A;
-            pB[e] = B;
-          } else {
-            pA[e] = slot_mul(pA[e], A, q == 0);
-            pB[e] = cmul(pB[e], B);
-          }
+      for (int c = 0; c < CPT; ++c)
+        if (unsigned(ph[c]) < unsigned(sb)) atomicAdd(A + ph[c], pv[c]);
+      if (a.m.I[n] > int64_t(CPT) * NT) {
+        // entries beyond the prefetched chunk: load and scatter directly
+        const int64_t In = a.m.I[n];
+        const float *col = a.UT + a.ut_off[n] + r * In;
+        const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
+        const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
+        for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
+          const int hb = __ldg(hn + i);
+          const float v = __ldg(col + i);
+          if (unsigned(hb) < unsigned(sb)) atomicAdd(A + hb, __ldg(sn + i) < 0 ? -v : v);
         }
       }
+      // prefetch the next column while this one is transformed
+      if (n + 1 < N)
+        fetch(r, n + 1);
+      else if (r + 1 < r1)
+        fetch(r + 1, 0);
       __syncthreads();
-    }
-    const float lam = a.lambda ? __ldg(a.lambda + r) : 1.f;
+      fft_first_pass<LOG2M, NT>(A, sb, B);
+      __syncthreads();
+      for (int e = tid; e < sb / 4; e += NT)
+        reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+      fft_middle_passes<LOG2M, NT, 1>(B, tws);
+      fft_last_pass_unpack<LOG2M, NT>(B, tw, X);
 #pragma unroll
-    for (int e = 0; e < EP; ++e) {
-      accA[e].x = fmaf(lam, pA[e].x, accA[e].x);
-      accA[e].y = fmaf(lam, pA[e].y, accA[e].y);
-      accB[e].x = fmaf(lam, pB[e].x, accB[e].x);
-      accB[e].y = fmaf(lam, pB[e].y, accB[e].y);
+      for (int e = 0; e < EPS; ++e)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int q = 0; q < RL; ++q) {
+            if (n == 0) {
+              p[e][b][q] = X[e][b][q];
+            } else {
+              const bool packed = (b == 0 && q == 0 && tid + e * NT == 0);
+              p[e][b][q] = slot_mul(p[e][b][q], X[e][b][q], packed);
+            }
+          }
     }
+#pragma unroll
+    for (int e = 0; e < EPS; ++e)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+          float2 &acc = accS[((e * 2 + b) * RL + q) * NT + tid];
+          acc = cadd(acc, p[e][b][q]);
+        }
   }
 
   // publish the partial spectrum
   float2 *Gd = a.G + d * int64_t(M + 1);
 #pragma unroll
-  for (int e = 0; e < EP; ++e) {
-    const int q = tid + e * NT;
-    if (q < HALF) {
-      if (q == 0) {
-        atomicAdd(&Gd[0].x, accA[e].x);
-        atomicAdd(&Gd[M].x, accA[e].y);
-        atomicAdd(&Gd[HALF].x, accB[e].x);
-        atomicAdd(&Gd[HALF].y, accB[e].y);
-      } else {
-        atomicAdd(&Gd[q].x, accA[e].x);
-        atomicAdd(&Gd[q].y, accA[e].y);
-        atomicAdd(&Gd[M - q].x, accB[e].x);
-        atomicAdd(&Gd[M - q].y, accB[e].y);
+  for (int e = 0; e < EPS; ++e) {
+    if (LPs::SLOTS % NT != 0 && tid + e * NT >= LPs::SLOTS) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int q = 0; q < RL; ++q) {
+        const float2 v = accS[((e * 2 + b) * RL + q) * NT + tid];
+        const int k = last_pass_index<LOG2M, NT>(e, b, q);
+        if (k == 0) {
+          atomicAdd(&Gd[0].x, v.x);
+          atomicAdd(&Gd[M].x, v.y);
+        } else {
+          atomicAdd(&Gd[k], v);
+        }
       }
-    }
   }
   __threadfence();
   __syncthreads();
@@ -124,44 +201,46 @@ __global__ void __launch_bounds__(NT) cp_kernel(CpArgs a, const float2 *__restri
   __threadfence();
 
   // last CTA for sketch d: one inverse real FFT of the summed spectrum
-#pragma unroll
-  for (int e = 0; e < EP; ++e) {
-    const int q = tid + e * NT;
-    if (q < HALF) {
-      float2 A, B;
-      if (q == 0) {
-        A = make_float2(__ldcg(&Gd[0].x), __ldcg(&Gd[M].x));
-        B = __ldcg(&Gd[HALF]);
-      } else {
-        A = __ldcg(&Gd[q]);
-        B = __ldcg(&Gd[M - q]);
-      }
-      pack_pair_conj<LOG2M>(buf, q, A, B, tw);
+  for (int q = tid; q < HALF; q += NT) {
+    float2 Av, Bv;
+    if (q == 0) {
+      Av = make_float2(__ldcg(&Gd[0].x), __ldcg(&Gd[M].x));
+      Bv = __ldcg(&Gd[HALF]);
+    } else {
+      Av = __ldcg(&Gd[q]);
+      Bv = __ldcg(&Gd[M - q]);
     }
+    pack_pair_conj<LOG2M>(B, q, Av, Bv, tw);
   }
   __syncthreads();
-  block_fft<LOG2M, NT>(buf, tw);
+  block_fft<LOG2M, NT>(B, tw);
   const float sc = 1.0f / float(M);
   float *od = a.out + d * a.m.Jt;
+  float *Br = reinterpret_cast<float *>(B);
   for (int64_t j = tid; j < a.m.Jt; j += NT) {
-    const float v = bufr[real_off(int(j))];
+    const float v = Br[real_off(int(j))];
     od[j] = (j & 1) ? -v * sc : v * sc;
   }
   if (tid == 0) a.counter[d] = 0u;
 }
 
 template <int LOG2M>
-int launch_cp(fcs_ctx *ctx, CpArgs &a, int64_t groups) {
+int launch_cp(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
   constexpr int NT = fft_threads(LOG2M);
-  const size_t smem = sizeof(float2) * padded_len(1 << LOG2M);
-  auto kern = cp_kernel<LOG2M, NT>;
-  if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp)");
-  }
-  kern<<<dim3(unsigned(groups), unsigned(a.D)), NT, smem, ctx->stream>>>(a, ctx->twiddle);
-  return check_cuda(ctx, cudaGetLastError(), "cp_kernel");
+  const size_t smem = CpSmem<LOG2M, NT>::bytes(a.sb);
+  const int cpt = int((Imax + NT - 1) / NT);
+  auto go = [&](auto kern) -> int {
+    if (smem > 48 * 1024) {
+      cudaError_t e =
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp)");
+    }
+    kern<<<dim3(unsigned(groups), unsigned(a.D)), NT, smem, ctx->stream>>>(a, ctx->twiddle);
+    return check_cuda(ctx, cudaGetLastError(), "cp_kernel");
+  };
+  if (cpt <= 1) return go(cp_kernel<LOG2M, NT, 1>);
+  if (cpt <= 2) return go(cp_kernel<LOG2M, NT, 2>);
+  return go(cp_kernel<LOG2M, NT, 4>);       // larger modes add a direct tail loop
 }
 
 }  // namespace
@@ -187,8 +266,6 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
     if (!host_U[n]) return set_error(ctx, FCS_EINVAL, "U[%d] is NULL", n);
     if (host_ldU[n] < R)
       return set_error(ctx, FCS_EINVAL, "ldU[%d]=%lld < R", n, (long long)host_ldU[n]);
-    a.U[n] = host_U[n];
-    a.ldU[n] = host_ldU[n];
   }
   const int log2p = ilog2_ceil(a.m.Jt) < kMinLog2P ? kMinLog2P : ilog2_ceil(a.m.Jt);
   if (log2p > kMaxLog2P)
@@ -198,7 +275,6 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
   const int M = 1 << log2m;
   a.D = D;
   a.R = R;
-  a.lambda = lambda;
   a.h = h;
   a.s = s;
   a.out = out;
@@ -209,17 +285,36 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
   a.ranks_per_cta = (R + groups - 1) / groups;
   groups = (R + a.ranks_per_cta - 1) / a.ranks_per_cta;
 
-  const size_t gbytes = sizeof(float2) * size_t(D) * size_t(M + 1);
+  int64_t Imax = 0, Jmax = 0, utlen = 0;
+  for (int n = 0; n < N; ++n) {
+    a.ut_off[n] = utlen;
+    utlen += R * host_I[n];
+    if (host_I[n] > Imax) Imax = host_I[n];
+    if (host_J[n] > Jmax) Jmax = host_J[n];
+  }
+  a.sb = int((Jmax + 3) / 4 * 4);
+  const size_t gbytes = (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
+  const size_t cbytes = 256;
   void *ws = nullptr;
-  rc = ensure_workspace(ctx, gbytes + 64 * sizeof(unsigned), &ws);
+  rc = ensure_workspace(ctx, gbytes + cbytes + sizeof(float) * size_t(utlen), &ws);
   if (rc) return rc;
   a.G = static_cast<float2 *>(ws);
   a.counter = reinterpret_cast<unsigned *>(static_cast<char *>(ws) + gbytes);
+  float *UT = reinterpret_cast<float *>(static_cast<char *>(ws) + gbytes + cbytes);
+  a.UT = UT;
   DeviceGuard g(ctx->device);
-  rc = check_cuda(ctx, cudaMemsetAsync(ws, 0, gbytes + 64 * sizeof(unsigned), ctx->stream),
+  rc = check_cuda(ctx, cudaMemsetAsync(ws, 0, gbytes + cbytes, ctx->stream),
                   "cudaMemsetAsync(cp workspace)");
   if (rc) return rc;
+  for (int n = 0; n < N; ++n) {
+    dim3 grid(unsigned((host_I[n] + 31) / 32), unsigned((R + 31) / 32));
+    if (grid.y > 65535) return set_error(ctx, FCS_EUNSUPPORTED, "rank too large");
+    transpose_factors_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(
+        host_U[n], host_I[n], R, host_ldU[n], n == 0 ? lambda : nullptr, UT + a.ut_off[n]);
+    rc = check_cuda(ctx, cudaGetLastError(), "transpose_factors_kernel");
+    if (rc) return rc;
+  }
   rc = FCS_EUNSUPPORTED;
-  FCS_DISPATCH_LOG2M(log2m, rc = launch_cp<L>(ctx, a, groups));
+  FCS_DISPATCH_LOG2M(log2m, rc = launch_cp<L>(ctx, a, groups, Imax));
   return rc;
 }
