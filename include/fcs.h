@@ -129,6 +129,34 @@ int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
                   int64_t ldh, float *out);
 
 /*
+ * fcs_sketch_cp_noalloc -- fcs_sketch_cp for callers that cannot allocate
+ * device memory.  (The paper has no counterpart: this is a deployment
+ * variant.)  Some callers may not call cudaMalloc: code running inside a
+ * host framework that owns every device byte through its own pool, loops
+ * where the implicit device synchronisation of cudaMalloc / cudaFree would
+ * stall other work, and processes whose device memory is fixed at start-up.
+ * This entry point needs no fcs_ctx and allocates nothing: its scratch is a
+ * file-scope __device__ array of 4 MiB (plus a 256 KiB twiddle table) that
+ * every GPU loading the library holds until the process exits.
+ *   - Runs on the calling thread's current device, on `stream`.
+ *   - The first call on a device looks up the arrays' device addresses and
+ *     fills the twiddle table, synchronising `stream` once; make that first
+ *     call before any stream capture.
+ *   - Problems whose scratch D*(P/2+1)*8 + 512 + R*sum(I_n)*4 bytes exceed
+ *     4 MiB are rejected with FCS_ENOMEM_BUDGET (nothing is launched).
+ *   - All calls share the one array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and corrupt each other's results.
+ *     Each call clears the parts that must start at zero.
+ *   - err (may be NULL) receives a message of at most err_len bytes.
+ * Arguments and output otherwise as fcs_sketch_cp.
+ */
+int fcs_sketch_cp_noalloc(void *stream, int N, const int64_t *host_I,
+                          const int32_t *host_J, int64_t R, int D,
+                          const float *const *host_U, const int64_t *host_ldU,
+                          const float *lambda, const int32_t *h, const int8_t *s,
+                          int64_t ldh, float *out, char *err, size_t err_len);
+
+/*
  * fcs_contract -- sketched contractions of Sec. 4.1, one per batch item b:
  *  kind FCS_CONTRACT_ALL, eq. (T_uvw):
  *      raw[b][d] = < FCS_d(T), FCS_d(v_1 o ... o v_N) >, evaluated as

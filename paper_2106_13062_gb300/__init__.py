@@ -72,6 +72,11 @@ def lib() -> C.CDLL:
                 "fcs_sketch_cp": (C.c_int, [vp, C.c_int, i64p, i32p, C.c_int64,
                                             C.c_int, C.POINTER(C.c_void_p), i64p,
                                             vp, vp, vp, C.c_int64, vp]),
+                "fcs_sketch_cp_noalloc": (C.c_int, [vp, C.c_int, i64p, i32p,
+                                                    C.c_int64, C.c_int,
+                                                    C.POINTER(C.c_void_p), i64p,
+                                                    vp, vp, vp, C.c_int64, vp,
+                                                    C.c_char_p, C.c_size_t]),
                 "fcs_contract": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, i64p,
                                            i32p, C.c_int, vp, C.c_int64,
                                            C.POINTER(C.c_void_p), vp, vp,
@@ -96,8 +101,8 @@ def exported_symbols():
     """Names of the C entry points this binding expects libfcs.so to export."""
     return ["fcs_version", "fcs_create", "fcs_destroy", "fcs_set_stream",
             "fcs_last_error", "fcs_workspace_bytes", "fcs_make_hashes",
-            "fcs_sketch_dense", "fcs_sketch_cp", "fcs_contract", "fcs_recover",
-            "fcs_sketch_outer"]
+            "fcs_sketch_dense", "fcs_sketch_cp", "fcs_sketch_cp_noalloc",
+            "fcs_contract", "fcs_recover", "fcs_sketch_outer"]
 
 
 # ------------------------------------------------------------------ helpers
@@ -238,6 +243,38 @@ def fcs_sketch_cp(ctx: Context, U, lam, J, h, s, ldh: int = 0,
         ctx.handle, N, _arr(C.c_int64, [u.shape[0] for u in U]),
         _arr(C.c_int32, J), R, D, ptrs, _arr(C.c_int64, [u.stride(0) for u in U]),
         _ptr(lam), _ptr(h), _ptr(s), ldh, _ptr(out)))
+    return out
+
+
+def fcs_sketch_cp_noalloc(U, lam, J, h, s, ldh: int = 0,
+                          out: torch.Tensor | None = None):
+    """fcs_sketch_cp without a context and without device allocation inside
+    the library (scratch lives in a fixed 4 MiB device array; see
+    include/fcs.h).  Runs on torch's current device and stream.  The output
+    tensor is allocated here by torch unless `out` is given."""
+    _need(h, torch.int32, "h")
+    _need(s, torch.int8, "s")
+    N = len(U)
+    R = U[0].shape[1]
+    for k, u in enumerate(U):
+        _need(u, torch.float32, f"U[{k}]", contiguous=False)
+        if u.dim() != 2 or u.shape[1] != R or u.stride(1) != 1:
+            raise ValueError("each U_n must be I_n x R with unit column stride")
+    if lam is not None:
+        _need(lam, torch.float32, "lambda")
+    D = h.shape[0]
+    if out is None:
+        out = torch.empty((D, jtilde(J)), dtype=torch.float32, device=U[0].device)
+    _need(out, torch.float32, "out")
+    ptrs = (C.c_void_p * N)(*[u.data_ptr() for u in U])
+    err = C.create_string_buffer(256)
+    stream = torch.cuda.current_stream(U[0].device).cuda_stream
+    rc = lib().fcs_sketch_cp_noalloc(
+        C.c_void_p(stream), N, _arr(C.c_int64, [u.shape[0] for u in U]),
+        _arr(C.c_int32, J), R, D, ptrs, _arr(C.c_int64, [u.stride(0) for u in U]),
+        _ptr(lam), _ptr(h), _ptr(s), ldh, _ptr(out), err, 256)
+    if rc != FCS_OK:
+        raise FcsError(rc, err.value.decode(errors="replace"))
     return out
 
 

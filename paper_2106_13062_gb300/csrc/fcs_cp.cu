@@ -18,6 +18,9 @@
 // finish for sketch d (ticket counter) runs the one inverse real FFT and
 // writes FCS_d.  The next column's factor values and hashes are prefetched
 // into registers while the current column is transformed.
+#include <cstdarg>
+#include <mutex>
+
 #include "fcs_fft.cuh"
 
 namespace fcs {
@@ -316,5 +319,202 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
   }
   rc = FCS_EUNSUPPORTED;
   FCS_DISPATCH_LOG2M(log2m, rc = launch_cp<L>(ctx, a, groups, Imax));
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// fcs_sketch_cp_noalloc: the CP-route sketch for callers that cannot allocate
+// device memory.  It runs the same two kernels as fcs_sketch_cp, but its
+// scratch (spectrum accumulator, tickets, transposed factor columns) and its
+// twiddle table live in file-scope __device__ arrays of fixed size instead of
+// a context workspace, so the call makes no cudaMalloc / cudaFree and needs
+// no fcs_ctx.
+namespace fcs {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;   // 4 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+// One copy of each array exists on every GPU that loads the library and is
+// held until the process exits.  In host code these names are host-side
+// stand-ins, not device addresses: kernels get the addresses that
+// cudaGetSymbolAddress returns at set-up.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+__device__ __align__(256) float2 g_noalloc_twiddle[kTwN];
+
+struct NoAllocDevice {
+  bool ready;
+  unsigned char *scratch;
+  float2 *twiddle;
+  int sm_count;
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// tw[k] = exp(-2 pi i k / kTwN) in FP64, rounded to FP32.
+__global__ void noalloc_twiddle_kernel(float2 *tw) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < kTwN) {
+    double sn, cs;
+    sincospi(2.0 * double(k) / double(kTwN), &sn, &cs);
+    tw[k] = make_float2(float(cs), float(-sn));
+  }
+}
+
+int noalloc_fail(char *err, size_t n, int code, const char *fmt, ...) {
+  if (err && n) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(err, n, fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+// First call on a device (with that device current): look up the device
+// addresses of the static arrays and fill the twiddle table (the stream is
+// synchronised once so any later stream sees the table).
+int noalloc_setup(int dev, cudaStream_t st, NoAllocDevice **out, char *err, size_t n) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocDevice &s = g_noalloc_dev[dev];
+  if (!s.ready) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return noalloc_fail(err, n, FCS_ECUDA, "cudaGetSymbolAddress(scratch): %s",
+                          cudaGetErrorString(e));
+    s.scratch = static_cast<unsigned char *>(p);
+    e = cudaGetSymbolAddress(&p, g_noalloc_twiddle);
+    if (e != cudaSuccess)
+      return noalloc_fail(err, n, FCS_ECUDA, "cudaGetSymbolAddress(twiddle): %s",
+                          cudaGetErrorString(e));
+    s.twiddle = static_cast<float2 *>(p);
+    e = cudaDeviceGetAttribute(&s.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+      return noalloc_fail(err, n, FCS_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+    noalloc_twiddle_kernel<<<kTwN / 256, 256, 0, st>>>(s.twiddle);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+      return noalloc_fail(err, n, FCS_ECUDA, "twiddle set-up: %s", cudaGetErrorString(e));
+    s.ready = true;
+  }
+  *out = &s;
+  return FCS_OK;
+}
+
+template <int LOG2M>
+int noalloc_launch_cp(CpArgs &a, int64_t groups, int64_t Imax, const float2 *tw,
+                      cudaStream_t st, char *err, size_t n) {
+  constexpr int NT = fft_threads(LOG2M);
+  const size_t smem = CpSmem<LOG2M, NT>::bytes(a.sb);
+  const int cpt = int((Imax + NT - 1) / NT);
+  auto go = [&](auto kern) -> int {
+    if (smem > 48 * 1024) {
+      cudaError_t e =
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess)
+        return noalloc_fail(err, n, FCS_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    }
+    kern<<<dim3(unsigned(groups), unsigned(a.D)), NT, smem, st>>>(a, tw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+      return noalloc_fail(err, n, FCS_ECUDA, "cp_kernel: %s", cudaGetErrorString(e));
+    return FCS_OK;
+  };
+  if (cpt <= 1) return go(cp_kernel<LOG2M, NT, 1>);
+  if (cpt <= 2) return go(cp_kernel<LOG2M, NT, 2>);
+  return go(cp_kernel<LOG2M, NT, 4>);
+}
+
+}  // namespace
+}  // namespace fcs
+
+extern "C" int fcs_sketch_cp_noalloc(void *stream, int N, const int64_t *host_I,
+                                     const int32_t *host_J, int64_t R, int D,
+                                     const float *const *host_U, const int64_t *host_ldU,
+                                     const float *lambda, const int32_t *h, const int8_t *s,
+                                     int64_t ldh, float *out, char *err, size_t err_len) {
+  if (err && err_len) err[0] = '\0';
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CpArgs a{};
+  if (make_modes(nullptr, N, host_I, host_J, ldh, &a.m) != FCS_OK)
+    return noalloc_fail(err, err_len, FCS_EINVAL,
+                        "invalid N, I_n, J_n or ldh (1 <= N <= %d, I_n >= 1, J_n >= 1)", kMaxN);
+  if (D < 1 || D > kMaxD)
+    return noalloc_fail(err, err_len, FCS_EINVAL, "D=%d outside [1,%d]", D, kMaxD);
+  if (R < 1) return noalloc_fail(err, err_len, FCS_EINVAL, "R=%lld must be >= 1", (long long)R);
+  if (!host_U || !host_ldU || !h || !s || !out)
+    return noalloc_fail(err, err_len, FCS_EINVAL, "NULL pointer argument");
+  for (int n = 0; n < N; ++n) {
+    if (!host_U[n]) return noalloc_fail(err, err_len, FCS_EINVAL, "U[%d] is NULL", n);
+    if (host_ldU[n] < R)
+      return noalloc_fail(err, err_len, FCS_EINVAL, "ldU[%d]=%lld < R", n,
+                          (long long)host_ldU[n]);
+  }
+  const int log2p = ilog2_ceil(a.m.Jt) < kMinLog2P ? kMinLog2P : ilog2_ceil(a.m.Jt);
+  if (log2p > kMaxLog2P)
+    return noalloc_fail(err, err_len, FCS_EUNSUPPORTED, "Jt=%lld needs FFT length > %d",
+                        (long long)a.m.Jt, 1 << kMaxLog2P);
+  const int log2m = log2p - 1;
+  const int M = 1 << log2m;
+  int64_t Imax = 0, Jmax = 0, utlen = 0;
+  for (int n = 0; n < N; ++n) {
+    a.ut_off[n] = utlen;
+    utlen += R * host_I[n];
+    if (host_I[n] > Imax) Imax = host_I[n];
+    if (host_J[n] > Jmax) Jmax = host_J[n];
+  }
+  const size_t gbytes = (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
+  const size_t cbytes = 256;
+  const size_t need = gbytes + cbytes + sizeof(float) * size_t(utlen);
+  if (need > kNoAllocScratchBytes)
+    return noalloc_fail(err, err_len, FCS_ENOMEM_BUDGET,
+                        "problem needs %zu bytes of scratch; the static scratch array holds "
+                        "%zu bytes (D*(P/2+1)*8 + R*sum(I_n)*4 must fit)",
+                        need, kNoAllocScratchBytes);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess)
+    return noalloc_fail(err, err_len, FCS_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return noalloc_fail(err, err_len, FCS_EUNSUPPORTED, "device %d beyond %d", dev,
+                        kNoAllocMaxDevices);
+  NoAllocDevice *sd = nullptr;
+  int rc = noalloc_setup(dev, st, &sd, err, err_len);
+  if (rc) return rc;
+
+  a.D = D;
+  a.R = R;
+  a.h = h;
+  a.s = s;
+  a.out = out;
+  a.sb = int((Jmax + 3) / 4 * 4);
+  int64_t groups = (int64_t(sd->sm_count) + D - 1) / D;
+  if (groups < 1) groups = 1;
+  if (groups > R) groups = R;
+  a.ranks_per_cta = (R + groups - 1) / groups;
+  groups = (R + a.ranks_per_cta - 1) / a.ranks_per_cta;
+  a.G = reinterpret_cast<float2 *>(sd->scratch);
+  a.counter = reinterpret_cast<unsigned *>(sd->scratch + gbytes);
+  float *UT = reinterpret_cast<float *>(sd->scratch + gbytes + cbytes);
+  a.UT = UT;
+  // the accumulator and tickets must start at zero; the array keeps the
+  // previous call's contents otherwise
+  e = cudaMemsetAsync(sd->scratch, 0, gbytes + cbytes, st);
+  if (e != cudaSuccess)
+    return noalloc_fail(err, err_len, FCS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  for (int n = 0; n < N; ++n) {
+    dim3 grid(unsigned((host_I[n] + 31) / 32), unsigned((R + 31) / 32));
+    if (grid.y > 65535) return noalloc_fail(err, err_len, FCS_EUNSUPPORTED, "rank too large");
+    transpose_factors_kernel<<<grid, dim3(32, 8), 0, st>>>(
+        host_U[n], host_I[n], R, host_ldU[n], n == 0 ? lambda : nullptr, UT + a.ut_off[n]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+      return noalloc_fail(err, err_len, FCS_ECUDA, "transpose: %s", cudaGetErrorString(e));
+  }
+  rc = FCS_EUNSUPPORTED;
+  FCS_DISPATCH_LOG2M(log2m, rc = noalloc_launch_cp<L>(a, groups, Imax, sd->twiddle, st, err,
+                                                      err_len));
   return rc;
 }
