@@ -1,13 +1,22 @@
 """Benchmark of the Fast Count Sketch hot path on GB300.
 
-Default workload (one step): CP-route FCS of one order-3 CP tensor,
+Default workload `cp` (one step): CP-route FCS of one order-3 CP tensor,
 I_n = 1000, rank R = 100, factors N(0,1), weights U(0.5, 1.5), J_n = 5000
 (Jt = 14998, FFT length 16384), D = 10 independent sketches -- the hash
-tables are generated on the device (fcs_make_hashes) and the sketches
-computed (fcs_sketch_cp).  Throughput unit: sketches/s (one sketch = one
-FCS_d vector of length Jt, so a step yields D sketches).
+tables are generated on the device (fcs_make_hashes) and the sketches computed
+(fcs_sketch_cp).  Unit: sketches/s (one sketch = one FCS_d vector of length
+Jt, so a step yields D sketches).
+
+Other workloads (`--workload`, not the default line):
+  dense  the robust-tensor-power-method step: dense-route FCS of a symmetric
+         500^3 FP32 tensor (rank 10, noise 0.01), J_n = 2000, D = 5, then
+         T(u,u,u) and T(I,u,u) for 64 unit vectors with the median over D.
+  kron   Kronecker compression: 32 pairs of 512x512 matrices, order-4 hashes
+         J_n = 1024, D = 10; sketch every A and B (dense route, batched),
+         combine FCS(A o B) by FFT, recover 2^20 sampled entries per pair.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fcs|reference]
+                    [--workload cp|dense|kron]
 
 N > 1 runs under torch.distributed.run as independent replicas (the path has
 no exchange step); `value` is the sketches all ranks produced divided by the
@@ -19,9 +28,11 @@ Prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -36,38 +47,41 @@ if ROOT not in sys.path:
 
 import synth  # noqa: E402
 
-WORKLOAD = {"workload": "cp_fcs_order3_I1000_R100_J5000_D10", "order": 3,
-            "I": 1000, "R": 100, "J": 5000, "D": 10, "seed": 2}
-METRIC = "FCS sketches/s (CP route, order 3, I=1000, R=100, J=5000, D=10)"
 L2_FLUSH_BYTES = 256 << 20
-
-
-def jt_of(w):
-    return w["order"] * w["J"] - w["order"] + 1
+CSRC = os.path.join(ROOT, "paper_2106_13062_gb300", "csrc")
 
 
 def fft_len(jt):
     return 1 << max(4, math.ceil(math.log2(jt)))
 
 
-def cp_flops(w):
-    """Algorithmic flops of one fcs_sketch_cp launch: 2.5 P log2 P per real
-    FFT of length P (D*R*N forward + D inverse) plus the pointwise mode
-    products and rank accumulation (6 flops per complex multiply, 4 per
-    real-weighted complex accumulate) over P/2+1 bins."""
-    N, R, D = w["order"], w["R"], w["D"]
-    P = fft_len(jt_of(w))
-    fft = D * (R * N + 1) * 2.5 * P * math.log2(P)
-    pointwise = D * R * (P // 2 + 1) * (6 * (N - 1) + 4)
-    return fft + pointwise
+def jt_of(J):
+    return int(sum(J) - len(J) + 1)
 
 
-def cp_bytes(w):
-    """Algorithmic bytes of one step: factors and weights read once, hash
-    tables written once (by fcs_make_hashes) and read once, sketches
-    written once."""
-    N, I, R, D = w["order"], w["I"], w["R"], w["D"]
-    return N * I * R * 4 + R * 4 + 2 * D * N * I * 5 + D * jt_of(w) * 4
+def sources_digest(files):
+    """sha256 over the kernel's source files (to tell whether an ncu capture
+    still describes the current kernel)."""
+    hsh = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:16]
+
+
+def profiled_traffic(profile_name, files):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    summary is absent or the kernel's sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", profile_name)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m1 = re.search(r"dram_bytes_per_launch\s*=\s*([0-9.eE+]+)", text)
+    m2 = re.search(r"sources_sha256\s*=\s*([0-9a-f]+)", text)
+    if not (m1 and m2) or m2.group(1) != sources_digest(files):
+        return None
+    return float(m1.group(1))
 
 
 # ------------------------------------------------------------------ clocks
@@ -122,30 +136,6 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-# ------------------------------------------------------------------ CPU oracle
-def oracle_sample(w, budget_s: float = 12.0):
-    """Time the FP64 oracle (CP route by direct convolution) on a bounded
-    sample of the workload: sketch d = 0 over the first R_s ranks, R_s grown
-    until about `budget_s` seconds.  Returns (sketches/s, R_s, seconds)."""
-    import oracle
-    N, I, R, J = w["order"], w["I"], w["R"], w["J"]
-    U, lam = synth.cp_factors(w["seed"], [I] * N, R)
-    h, s = oracle.make_hashes(w["seed"], [I] * N, [J] * N, 1)
-    Ud = [u.astype(np.float64) for u in U]
-    lamd = lam.astype(np.float64)
-    rs, spent = 1, 0.0
-    while True:
-        t0 = time.perf_counter()
-        oracle.fcs_cp([u[:, :rs] for u in Ud], lamd[:rs], [J] * N, h, s)
-        dt = time.perf_counter() - t0
-        if dt * 2 > budget_s or rs >= R:
-            spent = dt
-            break
-        rs = min(R, max(rs + 1, int(rs * budget_s / max(dt, 1e-3) / 3)))
-    per_sketch = dt * R / rs
-    return 1.0 / per_sketch, rs, spent
-
-
 def omp_threads():
     v = os.environ.get("OMP_NUM_THREADS")
     if v and v.isdigit():
@@ -156,46 +146,407 @@ def omp_threads():
         return os.cpu_count() or 1
 
 
-# ------------------------------------------------------------------ arms
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ================================================================== workloads
+class CpWorkload:
+    """Order-3 CP tensor, I_n = 1000, R = 100, J_n = 5000, D = 10."""
+    name = "cp_fcs_order3_I1000_R100_J5000_D10"
+    metric = "FCS sketches/s (CP route, order 3, I=1000, R=100, J=5000, D=10)"
+    N, I, R, J, D, seed = 3, 1000, 100, 5000, 10, 2
+
+    def __init__(self):
+        self.Is, self.Js = [self.I] * self.N, [self.J] * self.N
+        self.Jt = jt_of(self.Js)
+        self.P = fft_len(self.Jt)
+
+    def config(self):
+        return {"workload": self.name, "order": self.N, "I": self.I, "R": self.R,
+                "J": self.J, "D": self.D, "Jt": self.Jt, "fft_len": self.P,
+                "seed": self.seed}
+
+    def sketches_per_step(self):
+        return self.D
+
+    def launches_per_step(self):
+        return 2 + self.N            # hashes, one transpose per mode, cp_kernel
+
+    def flops(self):
+        """2.5 P log2 P per real FFT of length P (D*R*N forward + D inverse)
+        plus the pointwise mode products and rank sum (6 flops per complex
+        multiply, 2 per complex add) over P/2+1 bins."""
+        P = self.P
+        fft = self.D * (self.R * self.N + 1) * 2.5 * P * math.log2(P)
+        pointwise = self.D * self.R * (P // 2 + 1) * (6 * (self.N - 1) + 2)
+        return fft + pointwise
+
+    def bytes(self):
+        """Factors and weights read once, hash tables (int32 + int8) read
+        once, sketches written once."""
+        return (self.N * self.I * self.R * 4 + self.R * 4 +
+                self.D * self.N * self.I * 5 + self.D * self.Jt * 4)
+
+    # -- device
+    def setup(self, fcs, ctx, dev):
+        import torch
+        U, lam = synth.cp_factors(self.seed, self.Is, self.R)
+        self.host = {"U": U, "lam": lam}
+        self.Ug = [torch.from_numpy(u).to(dev) for u in U]
+        self.lamg = torch.from_numpy(lam).to(dev)
+        self.out = torch.empty((self.D, self.Jt), dtype=torch.float32, device=dev)
+        self.fcs, self.ctx, self.dev = fcs, ctx, dev
+
+    def step(self, k, marks):
+        fcs = self.fcs
+        h, s = fcs.fcs_make_hashes(self.ctx, self.seed + k, self.Is, self.Js, self.D)
+        marks("cp_kernel")
+        fcs.fcs_sketch_cp(self.ctx, self.Ug, self.lamg, self.Js, h, s, out=self.out)
+        marks(None)
+
+    def e2e_prepare(self):
+        import torch
+        self.Uh = [torch.from_numpy(u).pin_memory() for u in self.host["U"]]
+        self.lamh = torch.from_numpy(self.host["lam"]).pin_memory()
+        self.outh = torch.empty((self.D, self.Jt), dtype=torch.float32).pin_memory()
+        self.Ud = [torch.empty_like(u) for u in self.Ug]
+        self.lamd = torch.empty_like(self.lamg)
+        return (sum(u.numel() * 4 for u in self.Uh) + self.lamh.numel() * 4,
+                self.outh.numel() * 4)
+
+    def e2e_step(self, k):
+        fcs = self.fcs
+        for dst, src in zip(self.Ud, self.Uh):
+            dst.copy_(src, non_blocking=True)
+        self.lamd.copy_(self.lamh, non_blocking=True)
+        h, s = fcs.fcs_make_hashes(self.ctx, self.seed + k, self.Is, self.Js, self.D)
+        fcs.fcs_sketch_cp(self.ctx, self.Ud, self.lamd, self.Js, h, s, out=self.out)
+        self.outh.copy_(self.out, non_blocking=True)
+
+    def check(self):
+        import torch
+        return bool(torch.isfinite(self.out).all())
+
+    def roofline(self, times_ms, props):
+        t = statistics.mean(times_ms["cp_kernel"])
+        sm_mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
+        peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+        ach = self.flops() / (t / 1e3) / 1e12
+        files = ["fcs_cp.cu", "fcs_fft.cuh", "fcs_internal.cuh"]
+        return {"kernel": "cp_kernel (fcs_sketch_cp: factor transpose + fused sketch)",
+                "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak,
+                "traffic": profiled_traffic("cp_kernel_order3_I1000_R100_J5000_D10.txt", files),
+                "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes "
+                               f"x 2 flop/FMA x {sm_mhz:.0f} MHz (recipe unit counts, max clock)",
+                "flops_per_launch": self.flops(), "avg_launch_ms": t,
+                "hbm_gbs_algorithmic": self.bytes() / (t / 1e3) / 1e9}
+
+    # -- oracle
+    def oracle_sample(self, budget_s=12.0):
+        """FP64 oracle (direct convolutions) on whole sketches d = 0, 1, ...
+        until about budget_s seconds have been spent."""
+        import oracle
+        U, lam = synth.cp_factors(self.seed, self.Is, self.R)
+        h, s = oracle.make_hashes(self.seed, self.Is, self.Js, self.D)
+        Ud = [u.astype(np.float64) for u in U]
+        lamd = lam.astype(np.float64)
+        t0 = time.perf_counter()
+        done = 0
+        while done < self.D:
+            oracle.fcs_cp(Ud, lamd, self.Js, h[done:done + 1], s[done:done + 1])
+            done += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = time.perf_counter() - t0
+        return done / dt, f"{done} whole sketch(es) (d = 0..{done - 1}, all {self.R} ranks), {dt:.1f} s"
+
+    def reference_setup(self):
+        import oracle
+        U, lam = synth.cp_factors(self.seed, self.Is, self.R)
+        self.rh, self.rs = oracle.make_hashes(self.seed, self.Is, self.Js, 1)
+        self.rU = [u.astype(np.float64) for u in U]
+        self.rlam = lam.astype(np.float64)
+
+    def reference_step(self, k):
+        """One rank's term of sketch d = 0 (three count sketches and two direct
+        FP64 convolutions); R such steps make one sketch."""
+        import oracle
+        r = k % self.R
+        oracle.fcs_cp([u[:, r:r + 1] for u in self.rU], self.rlam[r:r + 1], self.Js,
+                      self.rh, self.rs)
+        return 1.0 / self.R
+
+    reference_sample = "each step: one rank's term of sketch d=0 (3 count sketches + 2 direct FP64 convolutions); R steps = 1 sketch"
+
+
+class DenseWorkload:
+    """Robust tensor power method step: 500^3, J_n = 2000, D = 5, B = 64."""
+    name = "rtpm_step_dense_order3_I500_J2000_D5_B64"
+    metric = "FCS sketches/s (dense route 500^3, J=2000, D=5, + T(u,u,u), T(I,u,u) for 64 u)"
+    N, I, J, D, B, seed = 3, 500, 2000, 5, 64, 3
+
+    def __init__(self):
+        self.Is, self.Js = [self.I] * self.N, [self.J] * self.N
+        self.Jt = jt_of(self.Js)
+        self.P = fft_len(self.Jt)
+
+    def config(self):
+        return {"workload": self.name, "order": self.N, "I": self.I, "J": self.J,
+                "D": self.D, "vectors": self.B, "Jt": self.Jt, "fft_len": self.P,
+                "tensor": "symmetric rank 10, weights 10..1, noise sigma 0.01",
+                "seed": self.seed}
+
+    def sketches_per_step(self):
+        return self.D
+
+    def launches_per_step(self):
+        return 1 + 2 + 2 * 3         # hashes, zero + dense, 2 x (spectrum, contract, median)
+
+    def bytes(self):
+        """Dense kernel: the tensor read once, tables read once, sketches
+        written once."""
+        return self.I ** 3 * 4 + self.D * self.N * self.I * 5 + self.D * self.Jt * 4
+
+    def setup(self, fcs, ctx, dev):
+        import torch
+        T, _, _ = synth.rtpm_tensor(self.seed, I=self.I, R=10, sigma=0.01)
+        u = synth.unit_vectors(self.seed + 1, self.B, self.I)
+        self.host = {"T": T, "u": u}
+        self.Tg = torch.from_numpy(T).to(dev)
+        self.ug = torch.from_numpy(u).to(dev)
+        self.fT = torch.empty((self.D, self.Jt), dtype=torch.float32, device=dev)
+        self.fcs, self.ctx, self.dev = fcs, ctx, dev
+
+    def step(self, k, marks, T=None, u=None):
+        fcs = self.fcs
+        T = self.Tg if T is None else T
+        u = self.ug if u is None else u
+        h, s = fcs.fcs_make_hashes(self.ctx, self.seed + k, self.Is, self.Js, self.D)
+        marks("dense_kernel")
+        fcs.fcs_sketch_dense(self.ctx, T, self.Js, h, s, out=self.fT)
+        marks("contract")
+        a = fcs.fcs_contract(self.ctx, fcs.FCS_CONTRACT_ALL, self.fT, [u, u, u],
+                             self.Is, self.Js, h, s)
+        b = fcs.fcs_contract(self.ctx, fcs.FCS_CONTRACT_FREE, self.fT, [None, u, u],
+                             self.Is, self.Js, h, s, free_mode=0)
+        marks(None)
+        return a, b
+
+    def e2e_prepare(self):
+        import torch
+        self.Th = torch.from_numpy(self.host["T"]).pin_memory()
+        self.uh = torch.from_numpy(self.host["u"]).pin_memory()
+        self.Td = torch.empty_like(self.Tg)
+        self.ud = torch.empty_like(self.ug)
+        self.ah = torch.empty((self.B,), dtype=torch.float32).pin_memory()
+        self.bh = torch.empty((self.B, self.I), dtype=torch.float32).pin_memory()
+        return (self.Th.numel() * 4 + self.uh.numel() * 4,
+                self.ah.numel() * 4 + self.bh.numel() * 4)
+
+    def e2e_step(self, k):
+        self.Td.copy_(self.Th, non_blocking=True)
+        self.ud.copy_(self.uh, non_blocking=True)
+        a, b = self.step(k, lambda _: None, T=self.Td, u=self.ud)
+        self.ah.copy_(a, non_blocking=True)
+        self.bh.copy_(b, non_blocking=True)
+
+    def check(self):
+        import torch
+        return bool(torch.isfinite(self.fT).all())
+
+    def roofline(self, times_ms, props):
+        t = statistics.mean(times_ms["dense_kernel"])
+        peak = float(measured_peaks().get("hbm_gbs", 6787.6))
+        ach = self.bytes() / (t / 1e3) / 1e9
+        files = ["fcs_dense.cu", "fcs_internal.cuh"]
+        return {"kernel": "dense_kernel (fcs_sketch_dense, incl. output zeroing)",
+                "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak,
+                "traffic": profiled_traffic("dense_kernel_rtpm_I500_J2000_D5.txt", files),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)",
+                "bytes_per_launch": self.bytes(), "avg_launch_ms": t,
+                "contract_ms": statistics.mean(times_ms["contract"])}
+
+    def oracle_sample(self, budget_s=12.0):
+        """FP64 oracle dense route on leading slabs T[0:k] (all D sketches),
+        scaled by I/k to one step's sketches."""
+        import oracle
+        T, _, _ = synth.rtpm_tensor(self.seed, I=self.I, R=10, sigma=0.01)
+        h, s = oracle.make_hashes(self.seed, self.Is, self.Js, self.D)
+        k = 10
+        while True:
+            t0 = time.perf_counter()
+            sub = T[:k]
+            hs = np.concatenate([h[:, :k], h[:, self.I:]], axis=1)
+            ss = np.concatenate([s[:, :k], s[:, self.I:]], axis=1)
+            oracle.fcs_dense(sub, self.Js, hs, ss)
+            dt = time.perf_counter() - t0
+            if dt > budget_s / 4 or k >= self.I:
+                break
+            k = min(self.I, k * 4)
+        per_step = dt * self.I / k
+        return self.D / per_step, f"dense route on slabs T[0:{k}] of {self.I} (all {self.D} sketches), {dt:.1f} s, scaled x{self.I / k:.0f}"
+
+
+class KronWorkload:
+    """Kronecker compression: 32 pairs 512x512, J_n = 1024, D = 10, 2^20
+    recovered entries per pair."""
+    name = "kron_32pairs_512x512_J1024_D10_M1M"
+    metric = "FCS sketches/s (Kronecker compression, 32 pairs 512x512, J=1024, D=10, recover 2^20/pair)"
+    pairs, n, J, D, Msamp, seed = 32, 512, 1024, 10, 1 << 20, 4
+
+    def __init__(self):
+        self.I4, self.J4 = [self.n] * 4, [self.J] * 4
+        self.Ja = 2 * self.J - 1
+        self.Jt = jt_of(self.J4)
+
+    def config(self):
+        return {"workload": self.name, "pairs": self.pairs, "matrix": [self.n, self.n],
+                "J": self.J, "D": self.D, "Jt": self.Jt, "fft_len": fft_len(self.Jt),
+                "samples_per_pair": self.Msamp, "seed": self.seed}
+
+    def sketches_per_step(self):
+        return self.pairs * self.D     # FCS(A o B) sketches per step
+
+    def launches_per_step(self):
+        return 1 + 2 * 2 + 1 + 1       # hashes, 2 x (zero + dense), outer, recover
+
+    def bytes_recover(self):
+        return self.pairs * self.Msamp * (4 * 4 + 4)
+
+    def bytes_dense(self):
+        return 2 * self.pairs * self.n * self.n * 4 + 2 * self.D * 2 * self.n * 5 + \
+            2 * self.pairs * self.D * self.Ja * 4
+
+    def setup(self, fcs, ctx, dev):
+        import torch
+        A = synth.gaussian(self.seed, (self.pairs, self.n, self.n))
+        B = synth.gaussian(self.seed + 1, (self.pairs, self.n, self.n))
+        idx = np.stack([synth.sample_indices(self.seed + 2 + p, self.Msamp, self.I4)
+                        for p in range(self.pairs)])
+        self.host = {"A": A, "B": B, "idx": idx}
+        self.Ag = torch.from_numpy(A).to(dev)
+        self.Bg = torch.from_numpy(B).to(dev)
+        self.idxg = torch.from_numpy(idx).to(dev)
+        self.fa = torch.empty((self.pairs, self.D, self.Ja), dtype=torch.float32, device=dev)
+        self.fb = torch.empty_like(self.fa)
+        self.fcs, self.ctx, self.dev = fcs, ctx, dev
+
+    def step(self, k, marks, A=None, B=None, idx=None):
+        fcs = self.fcs
+        A = self.Ag if A is None else A
+        B = self.Bg if B is None else B
+        idx = self.idxg if idx is None else idx
+        h, s = fcs.fcs_make_hashes(self.ctx, self.seed + k, self.I4, self.J4, self.D)
+        ld = 4 * self.n
+        marks("dense_kernel")
+        fcs.fcs_sketch_dense(self.ctx, A, self.J4[:2], h[:, :2 * self.n],
+                             s[:, :2 * self.n], ldh=ld, batched=True, out=self.fa)
+        fcs.fcs_sketch_dense(self.ctx, B, self.J4[2:], h[:, 2 * self.n:],
+                             s[:, 2 * self.n:], ldh=ld, batched=True, out=self.fb)
+        marks("outer")
+        sk = fcs.fcs_sketch_outer(self.ctx, self.fa, self.fb)
+        marks("recover_kernel")
+        rec = fcs.fcs_recover(self.ctx, sk, self.I4, self.J4, h, s, idx)
+        marks(None)
+        self.sk = sk
+        return rec
+
+    def e2e_prepare(self):
+        import torch
+        self.Ah = torch.from_numpy(self.host["A"]).pin_memory()
+        self.Bh = torch.from_numpy(self.host["B"]).pin_memory()
+        self.ih = torch.from_numpy(self.host["idx"]).pin_memory()
+        self.Ad, self.Bd = torch.empty_like(self.Ag), torch.empty_like(self.Bg)
+        self.idd = torch.empty_like(self.idxg)
+        self.rh = torch.empty((self.pairs, self.Msamp), dtype=torch.float32).pin_memory()
+        return ((self.Ah.numel() + self.Bh.numel() + self.ih.numel()) * 4,
+                self.rh.numel() * 4)
+
+    def e2e_step(self, k):
+        self.Ad.copy_(self.Ah, non_blocking=True)
+        self.Bd.copy_(self.Bh, non_blocking=True)
+        self.idd.copy_(self.ih, non_blocking=True)
+        rec = self.step(k, lambda _: None, A=self.Ad, B=self.Bd, idx=self.idd)
+        self.rh.copy_(rec, non_blocking=True)
+
+    def check(self):
+        import torch
+        return bool(torch.isfinite(self.sk).all())
+
+    def roofline(self, times_ms, props):
+        peak = float(measured_peaks().get("hbm_gbs", 6787.6))
+        tr = statistics.mean(times_ms["recover_kernel"])
+        td = statistics.mean(times_ms["dense_kernel"])
+        if tr >= td:
+            name, t, by = "recover_kernel (fcs_recover, batched)", tr, self.bytes_recover()
+            prof, files = "recover_kernel_kron_D10_M1M.txt", ["fcs_recover.cu", "fcs_internal.cuh"]
+        else:
+            name, t, by = "dense_kernel (fcs_sketch_dense, batched A and B)", td, self.bytes_dense()
+            prof, files = "dense_kernel_kron_512x512_D10.txt", ["fcs_dense.cu", "fcs_internal.cuh"]
+        ach = by / (t / 1e3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak,
+                "unit": "GB/s", "frac": ach / peak,
+                "traffic": profiled_traffic(prof, files),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)",
+                "bytes_per_launch": by, "avg_launch_ms": t,
+                "dense_ms": td, "outer_ms": statistics.mean(times_ms["outer"]),
+                "recover_ms": tr}
+
+    def oracle_sample(self, budget_s=12.0):
+        """FP64 oracle for one pair: dense sketches of A and B, direct
+        convolution combine, recovery of a 2^16-entry sample; scaled to 32
+        pairs and 2^20 samples."""
+        import oracle
+        A = synth.gaussian(self.seed, (1, self.n, self.n))[0]
+        B = synth.gaussian(self.seed + 1, (1, self.n, self.n))[0]
+        idx = synth.sample_indices(self.seed + 2, 1 << 16, self.I4)
+        h, s = oracle.make_hashes(self.seed, self.I4, self.J4, self.D)
+        t0 = time.perf_counter()
+        fa = oracle.fcs_dense(A, self.J4[:2], h[:, :2 * self.n], s[:, :2 * self.n])
+        fb = oracle.fcs_dense(B, self.J4[2:], h[:, 2 * self.n:], s[:, 2 * self.n:])
+        sk = oracle.outer_combine(fa, fb)
+        t1 = time.perf_counter()
+        oracle.recover(sk, self.I4, self.J4, h, s, idx)
+        t2 = time.perf_counter()
+        per_pair = (t1 - t0) + (t2 - t1) * (self.Msamp / (1 << 16))
+        return self.D / per_pair, f"one pair: dense sketches + combine ({t1 - t0:.2f} s) and 2^16 recoveries ({t2 - t1:.2f} s), scaled to 2^20"
+
+
+WORKLOADS = {"cp": CpWorkload, "dense": DenseWorkload, "kron": KronWorkload}
+
+
+# ================================================================== arms
 def run_reference(args, rank, world):
-    """The oracle timed as the reference arm: each step computes one rank's
-    contribution to one sketch (CS of three columns, two direct FP64
-    convolutions); throughput scales that to sketches/s."""
-    import oracle
+    """The FP64 oracle as the reference arm, on the host cores, rank 0 only."""
     if rank != 0:
         return None
-    w = WORKLOAD
-    N, I, R, J = w["order"], w["I"], w["R"], w["J"]
-    U, lam = synth.cp_factors(w["seed"], [I] * N, R)
-    h, s = oracle.make_hashes(w["seed"], [I] * N, [J] * N, 1)
-    Ud = [u.astype(np.float64) for u in U]
-    lamd = lam.astype(np.float64)
-
-    def step(k):
-        r = k % R
-        oracle.fcs_cp([u[:, r:r + 1] for u in Ud], lamd[r:r + 1], [J] * N, h, s)
-
+    w = WORKLOADS[args.workload]()
+    if not hasattr(w, "reference_step"):
+        return {"impl": "reference", "unavailable":
+                f"reference arm only defined for the default workload (cp), not {args.workload}"}
+    w.reference_setup()
     for k in range(args.warmup):
-        step(k)
+        w.reference_step(k)
     t0 = time.perf_counter()
+    units = 0.0
     for k in range(args.steps):
-        step(k)
+        units += w.reference_step(k)
     dt = time.perf_counter() - t0
-    ms = dt * 1e3 / args.steps
-    value = (args.steps / R) / dt
-    cores = omp_threads()
+    value = units / dt
     return {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "sketches/s",
+        "impl": "reference", "metric": w.metric, "value": value, "unit": "sketches/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(WORKLOAD, Jt=jt_of(w), fft_len=fft_len(jt_of(w)),
-                       parallelism="cpu oracle"),
-        "cpu_baseline": {"value": value, "unit": "sketches/s", "cores": cores,
-                         "kind": "oracle",
-                         "sample": f"each step: one rank's term of sketch d=0 "
-                                   f"(3 count sketches + 2 direct FP64 convolutions), "
-                                   f"{args.steps} steps = {args.steps / R:.2f} sketches"},
+        "config": dict(w.config(), parallelism="cpu oracle"),
+        "cpu_baseline": {"value": value, "unit": "sketches/s", "cores": omp_threads(),
+                         "kind": "oracle", "sample": w.reference_sample},
         "e2e": {"value": value, "unit": "sketches/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -207,130 +558,94 @@ def run_fcs(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = WORKLOAD
-    N, I, R, J, D = w["order"], w["I"], w["R"], w["J"], w["D"]
-    Is, Js = [I] * N, [J] * N
-    Jt = jt_of(w)
-    U, lam = synth.cp_factors(w["seed"], Is, R)
+    w = WORKLOADS[args.workload]()
     ctx = fcs.Context(local_rank)
-    Ug = [torch.from_numpy(u).to(dev) for u in U]
-    lamg = torch.from_numpy(lam).to(dev)
-    out = torch.empty((D, Jt), dtype=torch.float32, device=dev)
+    w.setup(fcs, ctx, dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(seed):
-        h, s = fcs.fcs_make_hashes(ctx, seed, Is, Js, D)
-        fcs.fcs_sketch_cp(ctx, Ug, lamg, Js, h, s, out=out)
-
     for k in range(args.warmup):
-        step(w["seed"] + k)
+        w.step(k, lambda _: None)
     torch.cuda.synchronize()
 
-    # ---- device-resident timed region
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # ---- device-resident timed region: per-step events, per-kernel marks
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    marks_all = []
     sampler = ClockSampler(local_rank)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
     for k in range(args.steps):
-        flush.zero_()                                    # L2 flush, untimed
-        e0, e1, e2 = ev[k]
-        e0.record(stream)
-        h, s = fcs.fcs_make_hashes(ctx, w["seed"] + k, Is, Js, D)
-        e1.record(stream)
-        fcs.fcs_sketch_cp(ctx, Ug, lamg, Js, h, s, out=out)
-        e2.record(stream)
+        flush.zero_()                                   # L2 flush, untimed
+        starts[k].record(stream)
+        marks = []
+
+        def mark(name, marks=marks):
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            marks.append((name, e))
+        w.step(args.warmup + k, mark)
+        ends[k].record(stream)
+        marks_all.append(marks)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if world > 1:
         torch.distributed.barrier()
-    step_ms = [a.elapsed_time(c) for a, b, c in ev]
-    cp_ms = [b.elapsed_time(c) for a, b, c in ev]
-    total_ms = sum(step_ms)
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    times = {}
+    for marks in marks_all:
+        for (name, e0), (_, e1) in zip(marks, marks[1:]):
+            times.setdefault(name, []).append(e0.elapsed_time(e1))
+    if not w.check():
+        raise RuntimeError("non-finite output")
 
-    # ---- end to end through the C ABI with host buffers
-    Uh = [torch.from_numpy(u).pin_memory() for u in U]
-    lamh = torch.from_numpy(lam).pin_memory()
-    outh = torch.empty((D, Jt), dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, min(args.steps, 200))
-    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(e2e_steps)]
-    Ud2 = [torch.empty_like(u) for u in Ug]
-    lam2 = torch.empty_like(lamg)
+    # ---- end to end with host buffers (inputs H2D and results D2H per step)
+    h2d, d2h = w.e2e_prepare()
+    e2e_steps = max(3, min(args.steps, 50 if args.workload != "cp" else 200))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(e2e_steps)]
     torch.cuda.synchronize()
     for k in range(e2e_steps):
         flush.zero_()
-        a, b = eev[k]
-        a.record(stream)
-        for dst, src in zip(Ud2, Uh):
-            dst.copy_(src, non_blocking=True)
-        lam2.copy_(lamh, non_blocking=True)
-        h, s = fcs.fcs_make_hashes(ctx, w["seed"] + k, Is, Js, D)
-        fcs.fcs_sketch_cp(ctx, Ud2, lam2, Js, h, s, out=out)
-        outh.copy_(out, non_blocking=True)
-        b.record(stream)
+        ev[k][0].record(stream)
+        w.e2e_step(k)
+        ev[k][1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in eev) / e2e_steps
-    h2d = sum(u.numel() * 4 for u in Uh) + lamh.numel() * 4
-    d2h = outh.numel() * 4
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ev) / e2e_steps
 
-    # correctness guard on the last device-timed output: finite values
-    if not torch.isfinite(out).all():
-        raise RuntimeError("non-finite sketch output")
-
-    # ---- max over ranks
     tmax = total_ms
     if world > 1:
         t = torch.tensor([total_ms, e2e_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         tmax, e2e_ms = float(t[0]), float(t[1])
+    props = torch.cuda.get_device_properties(local_rank)
+    roof = w.roofline(times, props)
     ctx.close()
     if rank != 0:
         return None
-
-    ms_per_step = tmax / args.steps
-    value = world * D * args.steps / (tmax / 1e3)
-    props = torch.cuda.get_device_properties(local_rank)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
-    cp_avg_ms = statistics.mean(cp_ms)
-    achieved = cp_flops(w) / (cp_avg_ms / 1e3) / 1e12
-    roof = {"kernel": "cp_kernel (fcs_sketch_cp)", "bound": "alu",
-            "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": None,
-            "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes "
-                           f"x 2 flop x {sm_mhz:.0f} MHz",
-            "flops_per_launch": cp_flops(w), "avg_launch_ms": cp_avg_ms,
-            "hbm_gbs_algorithmic": cp_bytes(w) / (cp_avg_ms / 1e3) / 1e9}
+    per_step = w.sketches_per_step()
     res = {
-        "impl": "fcs", "metric": METRIC, "value": value, "unit": "sketches/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "impl": "fcs", "metric": w.metric, "value": world * per_step * args.steps / (tmax / 1e3),
+        "unit": "sketches/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, Jt=Jt, fft_len=fft_len(Jt),
+        "config": dict(w.config(),
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                        l2="flushed between timed steps (256 MiB write)"),
         "roofline": roof,
-        "e2e": {"value": world * D / (e2e_ms / 1e3), "unit": "sketches/s",
+        "e2e": {"value": world * per_step / (e2e_ms / 1e3), "unit": "sketches/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": w.launches_per_step() * args.steps,
         "clocks": clocks,
+        "kernel_ms": {k: statistics.mean(v) for k, v in times.items()},
     }
     if world == 1 and not args.no_cpu_baseline:
-        v, rs, secs = oracle_sample(w)
+        v, sample = w.oracle_sample()
         res["cpu_baseline"] = {"value": v, "unit": "sketches/s", "cores": omp_threads(),
-                               "kind": "oracle",
-                               "sample": f"sketch d=0 over the first {rs} of {R} ranks "
-                                         f"({secs:.1f} s), scaled to one sketch"}
+                               "kind": "oracle", "sample": sample}
     return res
 
 
@@ -340,6 +655,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["fcs", "reference"], default="fcs")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cp")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -127,6 +127,24 @@ def _need(t: torch.Tensor, dtype, name: str, contiguous: bool = True):
     return t
 
 
+def _tables(h, s, ldh: int):
+    """Check the hash tables and return the sketch-row stride to pass: h and s
+    may be row-strided views (e.g. a run of modes of a wider table) as long as
+    both share the row stride and each row is contiguous."""
+    _need(h, torch.int32, "h", contiguous=False)
+    _need(s, torch.int8, "s", contiguous=False)
+    if h.dim() != 2 or s.shape != h.shape:
+        raise ValueError("h and s must both be [D, sum I]")
+    if h.stride(1) != 1 or s.stride(1) != 1:
+        raise ValueError("hash table rows must be contiguous")
+    if h.shape[0] > 1 and h.stride(0) != s.stride(0):
+        raise ValueError("h and s must share the row stride")
+    row = h.stride(0) if h.shape[0] > 1 else h.shape[1]
+    if ldh and h.shape[0] > 1 and ldh != row:
+        raise ValueError(f"ldh={ldh} disagrees with the tables' row stride {row}")
+    return ldh or (row if row != h.shape[1] else 0)
+
+
 def jtilde(J) -> int:
     """Sketch length of Def. 4: sum_n J_n - N + 1."""
     return int(sum(int(j) for j in J) - len(J) + 1)
@@ -198,8 +216,7 @@ def fcs_sketch_dense(ctx: Context, T: torch.Tensor, J, h, s, ldh: int = 0,
     Returns [D, Jt] (or [B, D, Jt])."""
     ctx._sync_stream()
     _need(T, torch.float32, "T", contiguous=False)
-    _need(h, torch.int32, "h")
-    _need(s, torch.int8, "s")
+    ldh = _tables(h, s, ldh)
     D = h.shape[0]
     Jt = jtilde(J)
     shape = list(T.shape[1:] if batched else T.shape)
@@ -223,8 +240,7 @@ def fcs_sketch_cp(ctx: Context, U, lam, J, h, s, ldh: int = 0,
     """Eq. (FCS_syn) CP-route FCS of [[lam; U_1..U_N]] (U_n: I_n x R FP32,
     row-major).  Returns [D, Jt]."""
     ctx._sync_stream()
-    _need(h, torch.int32, "h")
-    _need(s, torch.int8, "s")
+    ldh = _tables(h, s, ldh)
     N = len(U)
     R = U[0].shape[1]
     for k, u in enumerate(U):
@@ -252,8 +268,7 @@ def fcs_sketch_cp_noalloc(U, lam, J, h, s, ldh: int = 0,
     the library (scratch lives in a fixed 4 MiB device array; see
     include/fcs.h).  Runs on torch's current device and stream.  The output
     tensor is allocated here by torch unless `out` is given."""
-    _need(h, torch.int32, "h")
-    _need(s, torch.int8, "s")
+    ldh = _tables(h, s, ldh)
     N = len(U)
     R = U[0].shape[1]
     for k, u in enumerate(U):
@@ -286,8 +301,7 @@ def fcs_contract(ctx: Context, kind: int, fcsT: torch.Tensor, vecs, I, J, h, s,
     values ([B, D] or [B, D, I_m])."""
     ctx._sync_stream()
     _need(fcsT, torch.float32, "fcsT")
-    _need(h, torch.int32, "h")
-    _need(s, torch.int8, "s")
+    ldh = _tables(h, s, ldh)
     N = len(J)
     D = fcsT.shape[0]
     B = None
@@ -328,8 +342,7 @@ def fcs_recover(ctx: Context, sketch: torch.Tensor, I, J, h, s, idx: torch.Tenso
     ctx._sync_stream()
     _need(sketch, torch.float32, "sketch")
     _need(idx, torch.int32, "idx")
-    _need(h, torch.int32, "h")
-    _need(s, torch.int8, "s")
+    ldh = _tables(h, s, ldh)
     N = len(J)
     batched = sketch.dim() == 3
     nb = sketch.shape[0] if batched else 1

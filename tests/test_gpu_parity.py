@@ -403,10 +403,17 @@ def test_argument_errors(fcs, ctx):
     with pytest.raises(fcs.FcsError) as e:
         fcs.fcs_sketch_cp(ctx, U, None, [9000, 9000], h, s)
     assert e.value.code == fcs.FCS_EUNSUPPORTED
-    with pytest.raises(fcs.FcsError) as e:
+    with pytest.raises(ValueError):          # the binding checks the table stride
         fcs.fcs_sketch_dense(ctx, torch.randn(10, 10, device="cuda"), [5, 5], h, s,
                              ldh=3)
-    assert e.value.code == fcs.FCS_EINVAL
+    import ctypes as C                        # and so does the C entry point
+    T = torch.randn(10, 10, device="cuda")
+    out = torch.empty((2, 9), device="cuda")
+    rc = fcs.lib().fcs_sketch_dense(ctx.handle, 2, fcs._arr(C.c_int64, [10, 10]), None,
+                                    fcs._arr(C.c_int32, [5, 5]), 2, C.c_void_p(T.data_ptr()),
+                                    C.c_void_p(h.data_ptr()), C.c_void_p(s.data_ptr()), 3,
+                                    C.c_void_p(out.data_ptr()), 1, 0, 0)
+    assert rc == fcs.FCS_EINVAL
 
 
 def test_budget_zero_refuses_workspace(fcs):
