@@ -518,7 +518,150 @@ class KronWorkload:
         return self.D / per_pair, f"one pair: dense sketches + combine ({t1 - t0:.2f} s) and 2^16 recoveries ({t2 - t1:.2f} s), scaled to 2^20"
 
 
-WORKLOADS = {"cp": CpWorkload, "dense": DenseWorkload, "kron": KronWorkload}
+def mixed_cp_shapes(seed: int, count: int):
+    """Heterogeneous CP problems: order 3 or 4, I_n log-uniform in [50, 2000],
+    rank log-uniform in [1, 256], J_n log-uniform in [256, 8192] capped so that
+    Jt <= 16384, D uniform in 1..10."""
+    g = np.random.default_rng(seed)
+    shapes = []
+    for _ in range(count):
+        N = int(g.integers(3, 5))
+        I = [int(round(math.exp(g.uniform(math.log(50), math.log(2000))))) for _ in range(N)]
+        R = int(round(math.exp(g.uniform(0.0, math.log(256)))))
+        jmax = min(8192, (16384 + N - 1) // N)
+        J = [int(round(math.exp(g.uniform(math.log(256), math.log(jmax))))) for _ in range(N)]
+        D = int(g.integers(1, 11))
+        shapes.append((I, J, max(1, R), D))
+    return shapes
+
+
+class BatchWorkload:
+    """64 heterogeneous CP problems per step in one persistent launch (CUDA
+    graph replay of a prepared plan); the plain path runs one fcs_sketch_cp
+    per problem.  Unit: sketches/s."""
+    name = "batch_cp_mixed64"
+    metric = "FCS sketches/s (64 mixed CP problems per step, batched persistent launch)"
+    count, seed = 64, 5
+
+    def __init__(self):
+        self.shapes = mixed_cp_shapes(self.seed, self.count)
+
+    def config(self):
+        return {"workload": self.name, "problems": self.count,
+                "order": "3-4", "I": "log-U[50,2000]", "R": "log-U[1,256]",
+                "J": "log-U[256,8192], Jt<=16384", "D": "U{1..10}",
+                "sketches_per_step": self.sketches_per_step(), "seed": self.seed}
+
+    def sketches_per_step(self):
+        return sum(D for _, _, _, D in self.shapes)
+
+    def launches_per_step(self):
+        return 2                      # batched transpose + persistent kernel
+
+    def setup(self, fcs, ctx, dev):
+        import torch
+        self.fcs, self.ctx, self.dev = fcs, ctx, dev
+        self.items = []
+        probs = []
+        for k, (I, J, R, D) in enumerate(self.shapes):
+            U, lam = synth.cp_factors(self.seed * 1000 + k, I, R)
+            Ug = [torch.from_numpy(u).to(dev) for u in U]
+            lamg = torch.from_numpy(lam).to(dev)
+            h, s = fcs.fcs_make_hashes(ctx, k, I, J, D)
+            pr, out = fcs.cp_problem(Ug, lamg, J, h, s)
+            probs.append(pr)
+            self.items.append((Ug, lamg, h, s, out, J))
+        self.grain = fcs.fcs_batch_autotune(ctx, probs)
+        self.plan = fcs.BatchPlan(ctx, probs, grain=self.grain)
+        self.plan.launch()
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        st = torch.cuda.Stream(dev)
+        with torch.cuda.stream(st):
+            self.plan.launch()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(self.graph, stream=st):
+                self.plan.launch()
+        torch.cuda.synchronize()
+
+    def step(self, k, marks):
+        marks("batch_cp_kernel")
+        self.graph.replay()
+        marks(None)
+
+    def plain_step(self):
+        for Ug, lamg, h, s, out, J in self.items:
+            self.fcs.fcs_sketch_cp(self.ctx, Ug, lamg, J, h, s, out=out)
+
+    def e2e_prepare(self):
+        import torch
+        self.outh = [torch.empty(it[4].shape, dtype=torch.float32).pin_memory() for it in self.items]
+        self.Uh = [[u.cpu().pin_memory() for u in it[0]] for it in self.items]
+        return (sum(u.numel() * 4 for us in self.Uh for u in us),
+                sum(o.numel() * 4 for o in self.outh))
+
+    def e2e_step(self, k):
+        for it, us in zip(self.items, self.Uh):
+            for dst, src in zip(it[0], us):
+                dst.copy_(src, non_blocking=True)
+        self.graph.replay()
+        for it, oh in zip(self.items, self.outh):
+            oh.copy_(it[4], non_blocking=True)
+
+    def check(self):
+        import torch
+        return all(bool(torch.isfinite(it[4]).all()) for it in self.items)
+
+    def roofline(self, times_ms, props):
+        import torch
+        t = statistics.mean(times_ms["batch_cp_kernel"])
+        flops = 0.0
+        for I, J, R, D in self.shapes:
+            P = fft_len(jt_of(J))
+            flops += D * (R * len(I) + 1) * 2.5 * P * math.log2(P) + \
+                D * R * (P // 2 + 1) * (6 * (len(I) - 1) + 2)
+        # the plain path on the same problems, same stream, for comparison
+        stream = torch.cuda.current_stream(self.dev)
+        for _ in range(3):
+            self.plain_step()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(10):
+            self.plain_step()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        plain_ms = ev[0].elapsed_time(ev[1]) / 10
+        sm_mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
+        peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+        ach = flops / (t / 1e3) / 1e12
+        return {"kernel": "batch (transpose + persistent batch_cp_kernel, graph replay)",
+                "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes "
+                               f"x 2 flop/FMA x {sm_mhz:.0f} MHz",
+                "avg_launch_ms": t, "grain": self.grain,
+                "plain_per_problem_ms": plain_ms,
+                "plain_sketches_per_s": self.sketches_per_step() / (plain_ms / 1e3),
+                "batched_over_plain": plain_ms / t}
+
+    def oracle_sample(self, budget_s=12.0):
+        import oracle
+        t0 = time.perf_counter()
+        done = 0
+        for k, (I, J, R, D) in enumerate(self.shapes):
+            U, lam = synth.cp_factors(self.seed * 1000 + k, I, R)
+            h, s = oracle.make_hashes(k, I, J, 1)
+            oracle.fcs_cp([u.astype(np.float64) for u in U], lam.astype(np.float64), J, h, s)
+            done += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = time.perf_counter() - t0
+        return done / dt, f"sketch d=0 of the first {done} problems, {dt:.1f} s"
+
+
+WORKLOADS = {"cp": CpWorkload, "dense": DenseWorkload, "kron": KronWorkload,
+             "batch": BatchWorkload}
 
 
 # ================================================================== arms

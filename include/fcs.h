@@ -157,6 +157,61 @@ int fcs_sketch_cp_noalloc(void *stream, int N, const int64_t *host_I,
                           int64_t ldh, float *out, char *err, size_t err_len);
 
 /*
+ * Batched CP-route sketches.  (The paper sketches one tensor at a time; this
+ * is the batching layer over eq. (FCS_syn).)  Many CP tensors of uneven
+ * order, sizes, rank and sketch length run in one persistent launch: the
+ * work is cut into items (problem, sketch d, group of `grain` ranks), largest
+ * FFT first, and CTAs pull items from an atomic counter; the item that
+ * completes a sketch runs its inverse FFT.  Results equal fcs_sketch_cp on
+ * each problem up to FP32 summation order.
+ */
+typedef struct fcs_cp_problem {
+  int N;                    /* order, 1..8 */
+  int D;                    /* independent sketches, 1..16 */
+  int64_t R;                /* CP rank, >= 1 */
+  int64_t I[8];             /* mode sizes (first N used) */
+  int32_t J[8];             /* hash lengths (first N used) */
+  const float *U[8];        /* device: U_n, I_n x R row-major */
+  int64_t ldU[8];           /* leading dimensions, >= R */
+  const float *lambda;      /* device [R] or NULL (all ones) */
+  const int32_t *h;         /* device hash table [D][ldh] */
+  const int8_t *s;          /* device sign table [D][ldh] */
+  int64_t ldh;              /* 0 = sum I_n */
+  float *out;               /* device [D][Jt] */
+} fcs_cp_problem;
+
+typedef struct fcs_batch_plan fcs_batch_plan;
+
+/* Validate a batch, cut its items and upload descriptors into plan-owned
+ * device memory (counted against the context budget).  grain = ranks per
+ * item; 0 = the autotuned grain for this batch shape if fcs_batch_autotune
+ * has seen it (this context or the FCS_AUTOTUNE_CACHE file), else a default
+ * of about four items per SM.  The plan records the problems' device
+ * pointers: later launches read whatever those buffers hold then. */
+int fcs_batch_plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
+                          int grain, fcs_batch_plan **plan);
+
+/* Issue the batch on the context's stream: one memset, one batched factor
+ * transpose, one persistent kernel.  No allocation and no host
+ * synchronisation, so the call may be captured into a CUDA graph. */
+int fcs_batch_plan_launch(fcs_ctx *ctx, const fcs_batch_plan *plan);
+
+/* Release a plan (synchronises its context's stream first). */
+int fcs_batch_plan_destroy(fcs_batch_plan *plan);
+
+/* One-shot: create a plan, launch it, wait for it and release it. */
+int fcs_batch_sketch_cp(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
+                        int grain);
+
+/* Autotuner: time the whole batch on the device for grains 1, 2, 4, ...
+ * (up to 64 and 2R), keep the fastest for this batch shape (sorted
+ * (FFT length, N, D, R, max I_n) of every problem), write it to
+ * *host_best_grain and, when the environment variable FCS_AUTOTUNE_CACHE
+ * names a file, persist the table there. */
+int fcs_batch_autotune(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
+                       int *host_best_grain);
+
+/*
  * fcs_contract -- sketched contractions of Sec. 4.1, one per batch item b:
  *  kind FCS_CONTRACT_ALL, eq. (T_uvw):
  *      raw[b][d] = < FCS_d(T), FCS_d(v_1 o ... o v_N) >, evaluated as

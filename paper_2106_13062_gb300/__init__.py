@@ -87,6 +87,14 @@ def lib() -> C.CDLL:
                                           C.c_int64]),
                 "fcs_sketch_outer": (C.c_int, [vp, C.c_int64, C.c_int, C.c_int64,
                                                C.c_int64, vp, vp, vp]),
+                "fcs_batch_plan_create": (C.c_int, [vp, C.c_int, C.POINTER(CpProblem),
+                                                    C.c_int, C.POINTER(C.c_void_p)]),
+                "fcs_batch_plan_launch": (C.c_int, [vp, vp]),
+                "fcs_batch_plan_destroy": (C.c_int, [vp]),
+                "fcs_batch_sketch_cp": (C.c_int, [vp, C.c_int, C.POINTER(CpProblem),
+                                                  C.c_int]),
+                "fcs_batch_autotune": (C.c_int, [vp, C.c_int, C.POINTER(CpProblem),
+                                                 C.POINTER(C.c_int)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -97,12 +105,23 @@ def lib() -> C.CDLL:
     return _lib
 
 
+class CpProblem(C.Structure):
+    """Mirror of `fcs_cp_problem` (include/fcs.h)."""
+    _fields_ = [("N", C.c_int), ("D", C.c_int), ("R", C.c_int64),
+                ("I", C.c_int64 * 8), ("J", C.c_int32 * 8),
+                ("U", C.c_void_p * 8), ("ldU", C.c_int64 * 8),
+                ("lam", C.c_void_p), ("h", C.c_void_p), ("s", C.c_void_p),
+                ("ldh", C.c_int64), ("out", C.c_void_p)]
+
+
 def exported_symbols():
     """Names of the C entry points this binding expects libfcs.so to export."""
     return ["fcs_version", "fcs_create", "fcs_destroy", "fcs_set_stream",
             "fcs_last_error", "fcs_workspace_bytes", "fcs_make_hashes",
             "fcs_sketch_dense", "fcs_sketch_cp", "fcs_sketch_cp_noalloc",
-            "fcs_contract", "fcs_recover", "fcs_sketch_outer"]
+            "fcs_contract", "fcs_recover", "fcs_sketch_outer",
+            "fcs_batch_plan_create", "fcs_batch_plan_launch",
+            "fcs_batch_plan_destroy", "fcs_batch_sketch_cp", "fcs_batch_autotune"]
 
 
 # ------------------------------------------------------------------ helpers
@@ -382,3 +401,108 @@ def fcs_sketch_outer(ctx: Context, fa: torch.Tensor, fb: torch.Tensor):
     ctx.check(lib().fcs_sketch_outer(ctx.handle, nb, D, La, Lb, _ptr(fa),
                                      _ptr(fb), _ptr(out)))
     return out
+
+
+# ------------------------------------------------------------------ batching
+def cp_problem(U, lam, J, h, s, ldh: int = 0, out: torch.Tensor | None = None):
+    """Describe one CP-route sketch for the batch calls.  Returns the
+    `CpProblem` structure and its output tensor ([D, Jt], allocated here
+    unless given).  The caller keeps U, lam, h, s and out alive while any
+    plan built from the description may run."""
+    ldh = _tables(h, s, ldh)
+    N = len(U)
+    if N > 8:
+        raise ValueError("order > 8")
+    R = U[0].shape[1]
+    for k, u in enumerate(U):
+        _need(u, torch.float32, f"U[{k}]", contiguous=False)
+        if u.dim() != 2 or u.shape[1] != R or u.stride(1) != 1:
+            raise ValueError("each U_n must be I_n x R with unit column stride")
+    if lam is not None:
+        _need(lam, torch.float32, "lambda")
+    D = h.shape[0]
+    if out is None:
+        out = torch.empty((D, jtilde(J)), dtype=torch.float32, device=U[0].device)
+    _need(out, torch.float32, "out")
+    pr = CpProblem()
+    pr.N, pr.D, pr.R = N, D, R
+    for k in range(N):
+        pr.I[k] = U[k].shape[0]
+        pr.J[k] = int(J[k])
+        pr.U[k] = U[k].data_ptr()
+        pr.ldU[k] = U[k].stride(0)
+    pr.lam = None if lam is None else lam.data_ptr()
+    pr.h, pr.s, pr.ldh = h.data_ptr(), s.data_ptr(), ldh
+    pr.out = out.data_ptr()
+    return pr, out
+
+
+def _problem_array(problems):
+    arr = (CpProblem * len(problems))()
+    for k, pr in enumerate(problems):
+        arr[k] = pr
+    return arr
+
+
+class BatchPlan:
+    """A batch of CP-route sketches uploaded once (fcs_batch_plan_create);
+    `launch()` issues only device work on torch's current stream and may be
+    captured into a CUDA graph."""
+
+    def __init__(self, ctx: Context, problems, grain: int = 0):
+        self.ctx = ctx
+        self._arr = _problem_array(problems)
+        h = C.c_void_p()
+        ctx._sync_stream()
+        ctx.check(lib().fcs_batch_plan_create(ctx.handle, len(problems), self._arr,
+                                              grain, C.byref(h)))
+        self._h = h
+
+    def launch(self):
+        self.ctx._sync_stream()
+        self.ctx.check(lib().fcs_batch_plan_launch(self.ctx.handle, self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().fcs_batch_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fcs_batch_sketch_cp(ctx: Context, problems, grain: int = 0):
+    """One-shot batch of CP-route sketches (plan, launch, wait, release)."""
+    ctx._sync_stream()
+    arr = _problem_array(problems)
+    ctx.check(lib().fcs_batch_sketch_cp(ctx.handle, len(problems), arr, grain))
+
+
+def fcs_batch_autotune(ctx: Context, problems) -> int:
+    """Time the batch for each candidate grain and remember the best for this
+    batch shape; returns that grain."""
+    ctx._sync_stream()
+    arr = _problem_array(problems)
+    best = C.c_int(0)
+    ctx.check(lib().fcs_batch_autotune(ctx.handle, len(problems), arr, C.byref(best)))
+    return best.value
+
+
+def fcs_batch_plan_create(ctx: Context, problems, grain: int = 0) -> BatchPlan:
+    """C-ABI-named alias of BatchPlan(ctx, problems, grain)."""
+    return BatchPlan(ctx, problems, grain)
+
+
+def fcs_batch_plan_launch(ctx: Context, plan: BatchPlan):
+    """C-ABI-named alias of plan.launch() (ctx must be the plan's context)."""
+    if plan.ctx is not ctx:
+        raise ValueError("plan belongs to another context")
+    plan.launch()
+
+
+def fcs_batch_plan_destroy(plan: BatchPlan):
+    """C-ABI-named alias of plan.close()."""
+    plan.close()

@@ -1,0 +1,695 @@
+// fcs_batch.cu -- fcs_batch_sketch_cp / fcs_batch_autotune: many CP-route
+// sketches (eq. FCS_syn) of uneven order, sizes, rank and sketch length in one
+// persistent launch.
+//
+// Host side (fcs_batch_plan_create): the work is cut into items (problem p,
+// sketch d, group of `grain` ranks), ordered largest-FFT first, and uploaded
+// once with the problem descriptors into plan-owned device memory.  A launch
+// (fcs_batch_plan_launch) issues only device work -- clear the accumulators,
+// transpose every problem's factor columns in one batched launch, run the
+// persistent kernel -- so it can be captured into a CUDA graph and replayed.
+// Device side: a persistent kernel (one CTA per SM, 512 threads) pulls items
+// from an atomic counter.  Each item dispatches on its
+// problem's FFT length to the same block real FFT as fcs_sketch_cp (count
+// sketch into a compact shared buffer, Stockham passes, fused last pass and
+// unpack, mode product in registers, rank sum in shared memory), adds its
+// partial spectrum into the problem's accumulator, and the item that
+// completes sketch (p, d) (ticket counter) runs that sketch's inverse FFT.
+// The queue only counts up; no CTA ever waits on another.
+//
+// The grain (ranks per item) trades load balance against the number of
+// partial-spectrum flushes.  fcs_batch_autotune times the whole batch for
+// each candidate grain on the device and keeps the fastest per batch
+// signature (in the context, and in the file named by FCS_AUTOTUNE_CACHE
+// when that variable is set).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <array>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "fcs_fft.cuh"
+
+struct fcs_batch_state {
+  std::map<uint64_t, int> tuned;   // batch signature -> grain
+  bool cache_loaded = false;
+};
+
+struct fcs_batch_plan {
+  int device = 0;
+  void *dev = nullptr;             // descriptors, items, tasks, tickets, G, UT
+  size_t bytes = 0;
+  size_t clear_off = 0, clear_bytes = 0;
+  int nitems = 0, ntasks = 0, grid = 0;
+  int64_t tiles = 0;
+  size_t smem = 0;
+  size_t items_off = 0, tasks_off = 0;
+  fcs_ctx *owner = nullptr;
+};
+
+namespace fcs {
+namespace {
+
+constexpr int kBatchNT = 512;
+
+struct BatchProb {
+  int N, D, L, sb;
+  int64_t R, rpi;
+  int64_t I[kMaxN], off[kMaxN], ut_off[kMaxN];
+  int64_t ldh, Jt;
+  const float *UT;
+  const int32_t *h;
+  const int8_t *s;
+  float2 *G;
+  unsigned *tickets;
+  float *out;
+  int groups;
+  int pad_;
+};
+
+struct TransposeTask {
+  const float *U;
+  const float *lambda;
+  float *UT;
+  int64_t I, R, ld;
+  int64_t tiles_i, tile0;   // tiles along I; first flat tile index
+};
+
+// One CTA per 32x32 tile of one factor matrix; the task is found by binary
+// search over the tasks' first tile indices.
+__global__ void batch_transpose_kernel(const TransposeTask *__restrict__ tasks, int ntasks) {
+  __shared__ float tile[32][33];
+  const int64_t t = blockIdx.x;
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (tasks[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+  }
+  const TransposeTask T = tasks[lo];
+  const int64_t local = t - T.tile0;
+  const int64_t i0 = (local % T.tiles_i) * 32, r0 = (local / T.tiles_i) * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t i = i0 + k, r = r0 + threadIdx.x;
+    if (i < T.I && r < T.R) tile[k][threadIdx.x] = T.U[i * T.ld + r];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + k, i = i0 + threadIdx.x;
+    if (i < T.I && r < T.R) {
+      const float lam = T.lambda ? __ldg(T.lambda + r) : 1.f;
+      T.UT[r * T.I + i] = tile[threadIdx.x][k] * lam;
+    }
+  }
+}
+
+template <int L>
+struct BatchSmem {
+  static constexpr size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
+  static constexpr size_t kB = 0;
+  static constexpr size_t kAcc = up16(sizeof(float2) * padded_len(1 << L));
+  static constexpr size_t kTw = up16(kAcc + sizeof(float2) * LastPass<L, kBatchNT>::NV * kBatchNT);
+  static constexpr size_t kA = up16(kTw + sizeof(float2) * plan_twlen(L));
+  static size_t bytes(int sb) { return kA + sizeof(float) * size_t(sb); }
+};
+
+// One work item: ranks [r0, r1) of sketch d of problem P.
+template <int L>
+__device__ __noinline__ void batch_item(const BatchProb &P, int d, int64_t r0, int64_t r1,
+                           unsigned char *smem, const float2 *__restrict__ tw,
+                           bool fill_tw, int *s_flag) {
+  constexpr int NT = kBatchNT;
+  constexpr int CPT = 2;
+  using LPs = LastPass<L, NT>;
+  using Lay = BatchSmem<L>;
+  constexpr int M = 1 << L;
+  constexpr int HALF = M / 2;
+  constexpr int RL = LPs::RL, EPS = LPs::EPS, NV = LPs::NV;
+  float2 *B = reinterpret_cast<float2 *>(smem + Lay::kB);
+  float2 *accS = reinterpret_cast<float2 *>(smem + Lay::kAcc);
+  float2 *tws = reinterpret_cast<float2 *>(smem + Lay::kTw);
+  float *A = reinterpret_cast<float *>(smem + Lay::kA);
+  const int tid = threadIdx.x;
+  const int sb = P.sb;
+  const int N = P.N;
+
+  if (fill_tw) fill_twiddles<L, NT>(tws, tw);
+  for (int e = tid; e < sb / 4; e += NT)
+    reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) accS[v * NT + tid] = make_float2(0.f, 0.f);
+
+  float pv[CPT];
+  int ph[CPT];
+  auto fetch = [&](int64_t r, int n) {
+    const int64_t In = P.I[n];
+    const float *col = P.UT + P.ut_off[n] + r * In;
+    const int32_t *hn = P.h + d * P.ldh + P.off[n];
+    const int8_t *sn = P.s + d * P.ldh + P.off[n];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int64_t i = tid + int64_t(c) * NT;
+      ph[c] = -1;
+      pv[c] = 0.f;
+      if (i < In) {
+        const float v = __ldg(col + i);
+        pv[c] = __ldg(sn + i) < 0 ? -v : v;
+        ph[c] = __ldg(hn + i);
+      }
+    }
+  };
+  fetch(r0, 0);
+  __syncthreads();
+
+  float2 X[EPS][2][RL], p[EPS][2][RL];
+  for (int64_t r = r0; r < r1; ++r) {
+    for (int n = 0; n < N; ++n) {
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+        if (unsigned(ph[c]) < unsigned(sb)) atomicAdd(A + ph[c], pv[c]);
+      if (P.I[n] > int64_t(CPT) * NT) {
+        const int64_t In = P.I[n];
+        const float *col = P.UT + P.ut_off[n] + r * In;
+        const int32_t *hn = P.h + d * P.ldh + P.off[n];
+        const int8_t *sn = P.s + d * P.ldh + P.off[n];
+        for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
+          const int hb = __ldg(hn + i);
+          const float v = __ldg(col + i);
+          if (unsigned(hb) < unsigned(sb)) atomicAdd(A + hb, __ldg(sn + i) < 0 ? -v : v);
+        }
+      }
+      if (n + 1 < N)
+        fetch(r, n + 1);
+      else if (r + 1 < r1)
+        fetch(r + 1, 0);
+      __syncthreads();
+      fft_first_pass<L, NT>(A, sb, B);
+      __syncthreads();
+      for (int e = tid; e < sb / 4; e += NT)
+        reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+      fft_middle_passes<L, NT, 1>(B, tws);
+      fft_last_pass_unpack<L, NT>(B, tw, X);
+#pragma unroll
+      for (int e = 0; e < EPS; ++e)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int q = 0; q < RL; ++q) {
+            if (n == 0) {
+              p[e][b][q] = X[e][b][q];
+            } else {
+              const bool packed = (b == 0 && q == 0 && tid + e * NT == 0);
+              p[e][b][q] = slot_mul(p[e][b][q], X[e][b][q], packed);
+            }
+          }
+    }
+#pragma unroll
+    for (int e = 0; e < EPS; ++e)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+          float2 &acc = accS[((e * 2 + b) * RL + q) * NT + tid];
+          acc = cadd(acc, p[e][b][q]);
+        }
+  }
+
+  // publish the partial spectrum of sketch d
+  float2 *Gd = P.G + d * int64_t(M + 1);
+#pragma unroll
+  for (int e = 0; e < EPS; ++e) {
+    if (LPs::SLOTS % NT != 0 && tid + e * NT >= LPs::SLOTS) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int q = 0; q < RL; ++q) {
+        const float2 v = accS[((e * 2 + b) * RL + q) * NT + tid];
+        const int k = last_pass_index<L, NT>(e, b, q);
+        if (k == 0) {
+          atomicAdd(&Gd[0].x, v.x);
+          atomicAdd(&Gd[M].x, v.y);
+        } else {
+          atomicAdd(&Gd[k], v);
+        }
+      }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) *s_flag = (atomicAdd(&P.tickets[d], 1u) == unsigned(P.groups - 1));
+  __syncthreads();
+  if (*s_flag) {
+    __threadfence();
+    for (int q = tid; q < HALF; q += NT) {
+      float2 Av, Bv;
+      if (q == 0) {
+        Av = make_float2(__ldcg(&Gd[0].x), __ldcg(&Gd[M].x));
+        Bv = __ldcg(&Gd[HALF]);
+      } else {
+        Av = __ldcg(&Gd[q]);
+        Bv = __ldcg(&Gd[M - q]);
+      }
+      pack_pair_conj<L>(B, q, Av, Bv, tw);
+    }
+    __syncthreads();
+    block_fft<L, NT>(B, tw);
+    const float sc = 1.0f / float(M);
+    float *od = P.out + d * P.Jt;
+    const float *Br = reinterpret_cast<const float *>(B);
+    for (int64_t j = tid; j < P.Jt; j += NT) {
+      const float v = Br[real_off(int(j))];
+      od[j] = (j & 1) ? -v * sc : v * sc;
+    }
+    if (tid == 0) P.tickets[d] = 0u;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBatchNT, 1) batch_cp_kernel(const BatchProb *__restrict__ probs,
+                                                            const int4 *__restrict__ items,
+                                                            int nitems, unsigned *queue,
+                                                            const float2 *__restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item, s_flag;
+  int curL = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = int(atomicAdd(queue, 1u));
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const int4 w = items[it];
+    const BatchProb &P = probs[w.x];
+    const int64_t r0 = int64_t(w.z) * P.rpi;
+    const int64_t r1 = min(P.R, r0 + P.rpi);
+    const bool fill = P.L != curL;
+    curL = P.L;
+    switch (P.L) {
+#define FCS_BATCH_CASE(K) \
+  case K: batch_item<K>(P, w.y, r0, r1, smem, tw, fill, &s_flag); break;
+      FCS_BATCH_CASE(3) FCS_BATCH_CASE(4) FCS_BATCH_CASE(5) FCS_BATCH_CASE(6)
+      FCS_BATCH_CASE(7) FCS_BATCH_CASE(8) FCS_BATCH_CASE(9) FCS_BATCH_CASE(10)
+      FCS_BATCH_CASE(11) FCS_BATCH_CASE(12) FCS_BATCH_CASE(13)
+#undef FCS_BATCH_CASE
+      default:
+        break;
+    }
+  }
+}
+
+size_t batch_smem_bytes(int L, int sb) {
+  switch (L) {
+#define FCS_BS_CASE(K) \
+  case K: return BatchSmem<K>::bytes(sb);
+    FCS_BS_CASE(3) FCS_BS_CASE(4) FCS_BS_CASE(5) FCS_BS_CASE(6) FCS_BS_CASE(7)
+    FCS_BS_CASE(8) FCS_BS_CASE(9) FCS_BS_CASE(10) FCS_BS_CASE(11) FCS_BS_CASE(12)
+    FCS_BS_CASE(13)
+#undef FCS_BS_CASE
+    default:
+      return 0;
+  }
+}
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Per-problem facts derived on the host.
+struct HostProb {
+  Modes m;
+  int L, sb;
+  int64_t R, utlen, Imax;
+};
+
+int check_problem(fcs_ctx *ctx, int k, const fcs_cp_problem &q, HostProb *hp) {
+  int rc = make_modes(ctx, q.N, q.I, q.J, q.ldh, &hp->m);
+  if (rc) return set_error(ctx, rc, "problem %d: %s", k, ctx->err.c_str());
+  if (q.D < 1 || q.D > kMaxD) return set_error(ctx, FCS_EINVAL, "problem %d: D=%d", k, q.D);
+  if (q.R < 1) return set_error(ctx, FCS_EINVAL, "problem %d: R=%lld", k, (long long)q.R);
+  if (!q.h || !q.s || !q.out) return set_error(ctx, FCS_EINVAL, "problem %d: NULL pointer", k);
+  int64_t ut = 0, imax = 0, jmax = 0;
+  for (int n = 0; n < q.N; ++n) {
+    if (!q.U[n]) return set_error(ctx, FCS_EINVAL, "problem %d: U[%d] is NULL", k, n);
+    if (q.ldU[n] < q.R) return set_error(ctx, FCS_EINVAL, "problem %d: ldU[%d] < R", k, n);
+    ut += q.R * q.I[n];
+    imax = std::max<int64_t>(imax, q.I[n]);
+    jmax = std::max<int64_t>(jmax, q.J[n]);
+  }
+  int log2p = ilog2_ceil(hp->m.Jt);
+  if (log2p < kMinLog2P) log2p = kMinLog2P;
+  if (log2p > kMaxLog2P)
+    return set_error(ctx, FCS_EUNSUPPORTED, "problem %d: Jt=%lld needs FFT length > %d", k,
+                     (long long)hp->m.Jt, 1 << kMaxLog2P);
+  hp->L = log2p - 1;
+  hp->sb = int((jmax + 3) / 4 * 4);
+  hp->R = q.R;
+  hp->utlen = ut;
+  hp->Imax = imax;
+  return FCS_OK;
+}
+
+uint64_t batch_signature(int nprob, const std::vector<HostProb> &hp,
+                         const fcs_cp_problem *q) {
+  std::vector<std::array<int64_t, 5>> keys(nprob);
+  for (int k = 0; k < nprob; ++k)
+    keys[k] = {hp[k].L, q[k].N, q[k].D, hp[k].R, hp[k].Imax};
+  std::sort(keys.begin(), keys.end());
+  uint64_t x = 1469598103934665603ull;   // FNV-1a
+  auto mixin = [&](uint64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      x ^= (v >> (8 * b)) & 0xff;
+      x *= 1099511628211ull;
+    }
+  };
+  mixin(uint64_t(nprob));
+  for (auto &k : keys)
+    for (int64_t v : k) mixin(uint64_t(v));
+  return x;
+}
+
+void load_cache(fcs_batch_state &st) {
+  if (st.cache_loaded) return;
+  st.cache_loaded = true;
+  const char *path = getenv("FCS_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  unsigned long long sig;
+  int g;
+  while (fscanf(f, "%llx %d", &sig, &g) == 2) st.tuned[sig] = g;
+  fclose(f);
+}
+
+void save_cache(const fcs_batch_state &st) {
+  const char *path = getenv("FCS_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "w");
+  if (!f) return;
+  for (auto &kv : st.tuned) fprintf(f, "%016llx %d\n", (unsigned long long)kv.first, kv.second);
+  fclose(f);
+}
+
+int default_grain(const fcs_ctx *ctx, int nprob, const fcs_cp_problem *q) {
+  int64_t work = 0;
+  int64_t rmax = 1;
+  for (int k = 0; k < nprob; ++k) {
+    work += int64_t(q[k].D) * q[k].R;
+    rmax = std::max<int64_t>(rmax, q[k].R);
+  }
+  // about four items per SM, power-of-two grain
+  int64_t g = work / (4 * int64_t(std::max(1, ctx->sm_count)));
+  int grain = 1;
+  while (grain * 2 <= g && grain < 64) grain *= 2;
+  return int(std::min<int64_t>(grain, rmax));
+}
+
+// Build a plan: validate, cut items, lay out and upload the descriptors.
+int plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain,
+                fcs_batch_plan **out) {
+  *out = nullptr;
+  std::vector<HostProb> hp(nprob);
+  for (int k = 0; k < nprob; ++k) {
+    int rc = check_problem(ctx, k, q[k], &hp[k]);
+    if (rc) return rc;
+  }
+  std::vector<int4> items;
+  std::vector<BatchProb> probs(nprob);
+  int ntask = 0;
+  size_t g_bytes = 0, t_count = 0, ut_len = 0;
+  for (int k = 0; k < nprob; ++k) {
+    const int64_t rpi = std::min<int64_t>(std::max(grain, 1), hp[k].R);
+    const int groups = int((hp[k].R + rpi - 1) / rpi);
+    memset(&probs[k], 0, sizeof(BatchProb));
+    probs[k].rpi = rpi;
+    probs[k].groups = groups;
+    for (int d = 0; d < q[k].D; ++d)
+      for (int g = 0; g < groups; ++g) items.push_back(make_int4(k, d, g, 0));
+    g_bytes += up256(sizeof(float2) * size_t(q[k].D) * size_t((1 << hp[k].L) + 1));
+    t_count += size_t(q[k].D);
+    ut_len += size_t(hp[k].utlen);
+    ntask += q[k].N;
+  }
+  // largest FFT first, then the longest items (ranks x modes)
+  std::stable_sort(items.begin(), items.end(), [&](const int4 &x, const int4 &y) {
+    const int lx = hp[x.x].L, ly = hp[y.x].L;
+    if (lx != ly) return lx > ly;
+    return probs[x.x].rpi * q[x.x].N > probs[y.x].rpi * q[y.x].N;
+  });
+  const size_t b_probs = up256(sizeof(BatchProb) * nprob);
+  const size_t b_items = up256(sizeof(int4) * items.size());
+  const size_t b_tasks = up256(sizeof(TransposeTask) * ntask);
+  const size_t b_tick = up256(sizeof(unsigned) * (1 + t_count));
+  const size_t b_ut = up256(sizeof(float) * ut_len);
+  const size_t total = b_probs + b_items + b_tasks + b_tick + g_bytes + b_ut;
+  if (ctx->ws_bytes + ctx->plan_bytes + total > ctx->budget)
+    return set_error(ctx, FCS_ENOMEM_BUDGET,
+                     "batch plan of %zu bytes exceeds the context budget of %zu", total,
+                     ctx->budget);
+  fcs_batch_plan *plan = new (std::nothrow) fcs_batch_plan();
+  if (!plan) return set_error(ctx, FCS_ENOMEM_BUDGET, "out of host memory");
+  cudaError_t e = cudaMalloc(&plan->dev, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete plan;
+    return check_cuda(ctx, e, "cudaMalloc(batch plan)");
+  }
+  plan->bytes = total;
+  plan->device = ctx->device;
+  plan->owner = ctx;
+  char *base = static_cast<char *>(plan->dev);
+  unsigned *d_queue = reinterpret_cast<unsigned *>(base + b_probs + b_items + b_tasks);
+  char *g_base = base + b_probs + b_items + b_tasks + b_tick;
+  float *ut_base = reinterpret_cast<float *>(g_base + g_bytes);
+
+  std::vector<TransposeTask> tasks;
+  size_t goff = 0, toff = 1, uoff = 0, smem = 0;
+  int64_t tiles = 0;
+  for (int k = 0; k < nprob; ++k) {
+    BatchProb &P = probs[k];
+    P.N = q[k].N;
+    P.D = q[k].D;
+    P.L = hp[k].L;
+    P.sb = hp[k].sb;
+    P.R = hp[k].R;
+    for (int n = 0; n < kMaxN; ++n) {
+      P.I[n] = hp[k].m.I[n];
+      P.off[n] = hp[k].m.off[n];
+    }
+    P.ldh = hp[k].m.ldh;
+    P.Jt = hp[k].m.Jt;
+    P.h = q[k].h;
+    P.s = q[k].s;
+    P.out = q[k].out;
+    P.G = reinterpret_cast<float2 *>(g_base + goff);
+    goff += up256(sizeof(float2) * size_t(P.D) * size_t((1 << P.L) + 1));
+    P.tickets = d_queue + toff;
+    toff += size_t(P.D);
+    P.UT = ut_base + uoff;
+    int64_t local = 0;
+    for (int n = 0; n < P.N; ++n) {
+      P.ut_off[n] = local;
+      TransposeTask T;
+      T.U = q[k].U[n];
+      T.lambda = n == 0 ? q[k].lambda : nullptr;
+      T.UT = ut_base + uoff + local;
+      T.I = q[k].I[n];
+      T.R = P.R;
+      T.ld = q[k].ldU[n];
+      T.tiles_i = (T.I + 31) / 32;
+      T.tile0 = tiles;
+      tiles += T.tiles_i * ((T.R + 31) / 32);
+      tasks.push_back(T);
+      local += P.R * q[k].I[n];
+    }
+    uoff += size_t(local);
+    smem = std::max(smem, batch_smem_bytes(P.L, P.sb));
+  }
+  if (tiles > 0x7fffffffLL) {
+    cudaFree(plan->dev);
+    delete plan;
+    return set_error(ctx, FCS_EUNSUPPORTED, "batch too large");
+  }
+  std::vector<char> hb(b_probs + b_items + b_tasks, 0);
+  memcpy(hb.data(), probs.data(), sizeof(BatchProb) * nprob);
+  memcpy(hb.data() + b_probs, items.data(), sizeof(int4) * items.size());
+  memcpy(hb.data() + b_probs + b_items, tasks.data(), sizeof(TransposeTask) * tasks.size());
+  e = cudaMemcpy(base, hb.data(), hb.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(plan->dev);
+    delete plan;
+    return check_cuda(ctx, e, "cudaMemcpy(batch descriptors)");
+  }
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(batch_cp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(smem));
+    if (e != cudaSuccess) {
+      cudaFree(plan->dev);
+      delete plan;
+      return check_cuda(ctx, e, "cudaFuncSetAttribute(batch)");
+    }
+  }
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_cp_kernel, kBatchNT, smem);
+  if (per_sm < 1) per_sm = 1;
+  plan->nitems = int(items.size());
+  plan->ntasks = int(tasks.size());
+  plan->tiles = tiles;
+  plan->smem = smem;
+  plan->grid = std::max(1, std::min(plan->nitems, ctx->sm_count * per_sm));
+  plan->items_off = b_probs;
+  plan->tasks_off = b_probs + b_items;
+  plan->clear_off = b_probs + b_items + b_tasks;
+  plan->clear_bytes = b_tick + g_bytes;
+  ctx->plan_bytes += total;
+  *out = plan;
+  return FCS_OK;
+}
+
+// Device work only: capturable into a CUDA graph.
+int plan_launch(fcs_ctx *ctx, const fcs_batch_plan *plan) {
+  char *base = static_cast<char *>(plan->dev);
+  int rc = check_cuda(ctx, cudaMemsetAsync(base + plan->clear_off, 0, plan->clear_bytes,
+                                           ctx->stream),
+                      "cudaMemsetAsync(batch accumulators)");
+  if (rc) return rc;
+  batch_transpose_kernel<<<unsigned(plan->tiles), dim3(32, 8), 0, ctx->stream>>>(
+      reinterpret_cast<const TransposeTask *>(base + plan->tasks_off), plan->ntasks);
+  rc = check_cuda(ctx, cudaGetLastError(), "batch_transpose_kernel");
+  if (rc) return rc;
+  batch_cp_kernel<<<plan->grid, kBatchNT, plan->smem, ctx->stream>>>(
+      reinterpret_cast<const BatchProb *>(base),
+      reinterpret_cast<const int4 *>(base + plan->items_off), plan->nitems,
+      reinterpret_cast<unsigned *>(base + plan->clear_off), ctx->twiddle);
+  return check_cuda(ctx, cudaGetLastError(), "batch_cp_kernel");
+}
+
+void plan_free(fcs_batch_plan *plan) {
+  if (!plan) return;
+  if (plan->owner) plan->owner->plan_bytes -= plan->bytes;
+  if (plan->dev) cudaFree(plan->dev);
+  delete plan;
+}
+
+int resolve_grain(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain) {
+  if (grain > 0) return grain;
+  std::vector<HostProb> hp(nprob);
+  for (int k = 0; k < nprob; ++k)
+    if (check_problem(ctx, k, q[k], &hp[k]) != FCS_OK) return -1;
+  auto it = ctx->batch->tuned.find(batch_signature(nprob, hp, q));
+  return it != ctx->batch->tuned.end() ? it->second : default_grain(ctx, nprob, q);
+}
+
+}  // namespace
+}  // namespace fcs
+
+using namespace fcs;
+
+namespace fcs {
+void batch_state_destroy(fcs_ctx *ctx) {
+  if (ctx && ctx->batch) {
+    delete ctx->batch;
+    ctx->batch = nullptr;
+  }
+}
+}  // namespace fcs
+
+static int ensure_batch_state(fcs_ctx *ctx) {
+  if (!ctx->batch) {
+    ctx->batch = new (std::nothrow) fcs_batch_state();
+    if (!ctx->batch) return set_error(ctx, FCS_ENOMEM_BUDGET, "out of host memory");
+  }
+  load_cache(*ctx->batch);
+  return FCS_OK;
+}
+
+extern "C" int fcs_batch_plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
+                                     int grain, fcs_batch_plan **plan) {
+  if (!ctx || !plan) return FCS_EINVAL;
+  *plan = nullptr;
+  ctx->err.clear();
+  if (nprob < 1 || !host_probs) return set_error(ctx, FCS_EINVAL, "empty batch");
+  int rc = ensure_batch_state(ctx);
+  if (rc) return rc;
+  DeviceGuard g(ctx->device);
+  grain = resolve_grain(ctx, nprob, host_probs, grain);
+  if (grain < 1) return ctx->err.empty() ? set_error(ctx, FCS_EINVAL, "invalid batch") : FCS_EINVAL;
+  return plan_create(ctx, nprob, host_probs, grain, plan);
+}
+
+extern "C" int fcs_batch_plan_launch(fcs_ctx *ctx, const fcs_batch_plan *plan) {
+  if (!ctx || !plan) return FCS_EINVAL;
+  ctx->err.clear();
+  if (plan->owner != ctx) return set_error(ctx, FCS_EINVAL, "plan belongs to another context");
+  DeviceGuard g(ctx->device);
+  return plan_launch(ctx, plan);
+}
+
+extern "C" int fcs_batch_plan_destroy(fcs_batch_plan *plan) {
+  if (!plan) return FCS_OK;
+  DeviceGuard g(plan->device);
+  if (plan->owner) cudaStreamSynchronize(plan->owner->stream);
+  plan_free(plan);
+  return FCS_OK;
+}
+
+extern "C" int fcs_batch_sketch_cp(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
+                                   int grain) {
+  fcs_batch_plan *plan = nullptr;
+  int rc = fcs_batch_plan_create(ctx, nprob, host_probs, grain, &plan);
+  if (rc) return rc;
+  DeviceGuard g(ctx->device);
+  rc = plan_launch(ctx, plan);
+  cudaStreamSynchronize(ctx->stream);   // the plan's memory is released below
+  plan_free(plan);
+  return rc;
+}
+
+extern "C" int fcs_batch_autotune(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
+                                  int *host_best_grain) {
+  if (!ctx) return FCS_EINVAL;
+  ctx->err.clear();
+  if (nprob < 1 || !host_probs) return set_error(ctx, FCS_EINVAL, "empty batch");
+  int rc = ensure_batch_state(ctx);
+  if (rc) return rc;
+  DeviceGuard g(ctx->device);
+  std::vector<HostProb> hp(nprob);
+  int64_t rmax = 1;
+  for (int k = 0; k < nprob; ++k) {
+    rc = check_problem(ctx, k, host_probs[k], &hp[k]);
+    if (rc) return rc;
+    rmax = std::max<int64_t>(rmax, hp[k].R);
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return set_error(ctx, FCS_ECUDA, "cudaEventCreate");
+  int best = 1;
+  float best_ms = 1e30f;
+  for (int grain = 1; grain <= 64 && grain < 2 * rmax; grain *= 2) {
+    fcs_batch_plan *plan = nullptr;
+    rc = plan_create(ctx, nprob, host_probs, grain, &plan);
+    if (rc) break;
+    rc = plan_launch(ctx, plan);                        // warm-up
+    float total = 0.f;
+    for (int rep = 0; rep < 3 && rc == FCS_OK; ++rep) {
+      cudaEventRecord(e0, ctx->stream);
+      rc = plan_launch(ctx, plan);
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      total += ms;
+    }
+    cudaStreamSynchronize(ctx->stream);
+    plan_free(plan);
+    if (rc) break;
+    if (total < best_ms) {
+      best_ms = total;
+      best = grain;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  ctx->batch->tuned[batch_signature(nprob, hp, host_probs)] = best;
+  save_cache(*ctx->batch);
+  if (host_best_grain) *host_best_grain = best;
+  return FCS_OK;
+}

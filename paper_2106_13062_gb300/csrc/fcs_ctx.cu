@@ -142,6 +142,7 @@ extern "C" int fcs_destroy(fcs_ctx *ctx) {
   if (!ctx) return FCS_OK;
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  batch_state_destroy(ctx);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->twiddle) cudaFree(ctx->twiddle);
   delete ctx;

@@ -201,7 +201,6 @@ __device__ __forceinline__ void fft_last_pass_unpack(const float2 *B,
                                                      const float2 *__restrict__ tw,
                                                      float2 (*X)[2][LastPass<L, NT>::RL]) {
   using LPs = LastPass<L, NT>;
-  constexpr int M = 1 << L;
   constexpr int RL = LPs::RL, LRL = LPs::LRL, NS = LPs::NS;
 #pragma unroll
   for (int e = 0; e < LPs::EPS; ++e) {

@@ -30,6 +30,8 @@ struct fcs_ctx {
   float2 *twiddle = nullptr;     // kTwN entries: exp(-2 pi i k / kTwN)
   void *ws = nullptr;            // workspace, grown on demand
   size_t ws_bytes = 0;
+  size_t plan_bytes = 0;         // device bytes held by live batch plans
+  struct fcs_batch_state *batch = nullptr;   // autotune cache (fcs_batch.cu)
   std::string err;
 };
 
@@ -43,6 +45,7 @@ constexpr int kMaxLog2P = 14;          // FFT length P <= 16384
 constexpr int kMinLog2P = 4;
 
 int set_error(fcs_ctx *ctx, int code, const char *fmt, ...);
+void batch_state_destroy(fcs_ctx *ctx);
 int check_cuda(fcs_ctx *ctx, cudaError_t e, const char *what);
 // Grow the workspace to at least `bytes` (contents are not preserved).
 int ensure_workspace(fcs_ctx *ctx, size_t bytes, void **out);

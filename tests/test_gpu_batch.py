@@ -1,0 +1,134 @@
+"""Batched CP-route sketches: one persistent launch over problems of uneven
+order, sizes, rank and sketch length must give each problem's fcs_sketch_cp
+result (and the oracle's) within the sketch tolerance.  Needs a GPU."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_common import assert_sketch_close, cuda, host
+
+pytestmark = pytest.mark.gpu
+
+# (I, J, R, D): orders 1..4, FFT lengths 16 .. 16384
+SHAPES = [
+    ([20, 20, 20], [8, 8, 8], 5, 1),
+    ([300], [100], 4, 2),
+    ([64, 80], [600, 700], 9, 3),
+    ([10, 12, 9, 11], [50, 60, 70, 80], 3, 2),
+    ([5, 6, 7], [2, 3, 4], 2, 1),
+    ([200, 150, 300], [5000, 5000, 5000], 7, 4),
+    ([90, 70, 80], [1500, 1200, 1000], 33, 5),
+    ([1000, 700], [2000, 3000], 64, 10),
+]
+
+
+@pytest.fixture(scope="module")
+def fcs():
+    import paper_2106_13062_gb300 as m
+    m.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(fcs):
+    c = fcs.Context()
+    yield c
+    c.close()
+
+
+def _make(fcs, ctx, orc=None, seed=0):
+    probs, refs, keep = [], [], []
+    for k, (I, J, R, D) in enumerate(SHAPES):
+        U, lam = synth.cp_factors(seed + k, I, R)
+        Ug = [cuda(u) for u in U]
+        lamg = cuda(lam)
+        h, s = fcs.fcs_make_hashes(ctx, 100 + seed + k, I, J, D)
+        pr, out = fcs.cp_problem(Ug, lamg, J, h, s)
+        probs.append(pr)
+        refs.append(fcs.fcs_sketch_cp(ctx, Ug, lamg, J, h, s))
+        keep.append((U, lam, Ug, lamg, h, s, out, I, J))
+    return probs, refs, keep
+
+
+@pytest.mark.parametrize("grain", [0, 1, 3, 64])
+def test_batch_matches_single_problem_calls(fcs, ctx, grain):
+    probs, refs, keep = _make(fcs, ctx)
+    fcs.fcs_batch_sketch_cp(ctx, probs, grain=grain)
+    for k, ref in enumerate(refs):
+        assert_sketch_close(host(keep[k][6]), host(ref), what=f"problem {k}")
+
+
+def test_batch_matches_oracle(fcs, ctx, orc):
+    probs, refs, keep = _make(fcs, ctx, seed=7)
+    fcs.fcs_batch_sketch_cp(ctx, probs)
+    for k, (U, lam, Ug, lamg, h, s, out, I, J) in enumerate(keep):
+        if np.prod(I) * U[0].shape[1] > 5e7:
+            continue                       # the large ones are covered above
+        ref = orc.fcs_cp([u.astype(np.float64) for u in U], lam.astype(np.float64), J,
+                         host(h), host(s))
+        assert_sketch_close(host(out), ref, what=f"problem {k}")
+
+
+def test_plan_relaunch_and_graph_replay(fcs, ctx):
+    probs, refs, keep = _make(fcs, ctx, seed=3)
+    plan = fcs.BatchPlan(ctx, probs, grain=4)
+    plan.launch()
+    torch.cuda.synchronize()
+    first = [host(k[6]).copy() for k in keep]
+    for o in keep:
+        o[6].zero_()
+    plan.launch()                          # accumulators are cleared each launch
+    torch.cuda.synchronize()
+    for k, f in enumerate(first):
+        assert_sketch_close(host(keep[k][6]), f, what=f"relaunch {k}")
+    # capture one launch into a CUDA graph and replay it on new factor values
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        plan.launch()                      # warm the stream
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            plan.launch()
+    for k, item in enumerate(keep):
+        for u in item[2]:
+            u.mul_(-1.0)                   # new inputs in the same buffers
+        item[6].zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for k, item in enumerate(keep):
+        N = len(item[7])
+        sign = -1.0 if N % 2 else 1.0      # every factor negated: (-1)^N
+        assert_sketch_close(host(item[6]), sign * first[k], what=f"graph {k}")
+    plan.close()
+
+
+def test_autotune_and_cache_file(fcs, tmp_path):
+    path = str(tmp_path / "fcs_tune.txt")
+    os.environ["FCS_AUTOTUNE_CACHE"] = path
+    try:
+        c = fcs.Context()
+        probs, refs, keep = _make(fcs, c, seed=11)
+        g = fcs.fcs_batch_autotune(c, probs)
+        assert g in (1, 2, 4, 8, 16, 32, 64)
+        assert os.path.exists(path)
+        line = open(path).read().split()
+        assert int(line[1]) == g
+        fcs.fcs_batch_sketch_cp(c, probs)   # uses the tuned grain
+        for k, ref in enumerate(refs):
+            assert_sketch_close(host(keep[k][6]), host(ref), what=f"tuned {k}")
+        c.close()
+    finally:
+        del os.environ["FCS_AUTOTUNE_CACHE"]
+
+
+def test_batch_rejects_bad_problem(fcs, ctx):
+    probs, refs, keep = _make(fcs, ctx)
+    probs[2].R = 0
+    with pytest.raises(fcs.FcsError) as e:
+        fcs.fcs_batch_sketch_cp(ctx, probs)
+    assert e.value.code == fcs.FCS_EINVAL
