@@ -212,6 +212,92 @@ int fcs_batch_autotune(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs
                        int *host_best_grain);
 
 /*
+ * Request server with continuous batching.  (No counterpart in the paper:
+ * this is the serving layer over fcs_batch_* and fcs_contract.)
+ * Clients on any host thread submit requests; one scheduler thread owns the
+ * GPU.  It admits queued requests in FIFO order while in-flight slots, device
+ * arena memory and pinned staging memory allow, and issues each admitted
+ * group as one round on one of `streams` CUDA streams: host->device copies,
+ * hash generation, one batched launch for all CP requests of the round,
+ * contractions against resident sketches, device->host copies.  Several
+ * rounds run at once, so requests that arrive while others are on the GPU
+ * are admitted as soon as slots and memory free up and overlap with them.
+ * Host buffers named in a request must stay valid until it completes.
+ */
+#define FCS_REQ_CP 0          /* sketch a CP tensor given by host factors     */
+#define FCS_REQ_CONTRACT 1    /* contract vectors with a resident sketch      */
+
+typedef struct fcs_server fcs_server;
+
+typedef struct fcs_server_config {
+  int device;               /* CUDA device */
+  int streams;              /* rounds in flight at once, 1..8 */
+  int max_inflight;         /* admitted, not yet completed requests */
+  int max_batch;            /* CP requests per round */
+  size_t arena_bytes;       /* device arena: request data, plans, resident sketches */
+  size_t staging_bytes;     /* pinned host staging for copies and descriptors */
+  size_t workspace_bytes;   /* per-stream context workspace budget */
+} fcs_server_config;
+
+typedef struct fcs_request {
+  int kind;                 /* FCS_REQ_CP or FCS_REQ_CONTRACT */
+  int N;                    /* order */
+  int64_t I[8];             /* mode sizes */
+  int32_t J[8];             /* hash lengths */
+  /* FCS_REQ_CP */
+  int D;                    /* sketches */
+  int64_t R;                /* rank */
+  uint64_t seed;            /* hash seed (fcs_make_hashes) */
+  const float *host_U[8];   /* I_n x R row-major (leading dimension R) */
+  const float *host_lambda; /* [R] or NULL */
+  float *host_out;          /* [D][Jt] or NULL (then keep_resident must be 1) */
+  int keep_resident;        /* keep sketch and hash tables on the device */
+  /* FCS_REQ_CONTRACT */
+  int64_t sketch_id;        /* a resident sketch (same N, I, J) */
+  int contract_kind;        /* FCS_CONTRACT_ALL / FCS_CONTRACT_FREE */
+  int free_mode;
+  int64_t B;                /* vectors per mode */
+  const float *host_vecs[8];/* [B][I_n] (free mode's may be NULL) */
+  float *host_result;       /* [B] or [B][I_free] (median over D) */
+} fcs_request;
+
+typedef struct fcs_result {
+  int64_t ticket;
+  int state;                /* 0 queued, 1 running, 2 done, 3 failed, 4 cancelled */
+  int status;               /* FCS_* of the request once finished */
+  int64_t sketch_id;        /* CP with keep_resident: id for contractions */
+  double latency_s;         /* submit -> completion, -1 while unfinished */
+} fcs_result;
+
+typedef struct fcs_stats {
+  int64_t submitted, completed, failed, cancelled, rounds, sketches;
+  int64_t max_inflight_seen;
+  size_t arena_used;
+  double p50_latency_s, p99_latency_s, mean_latency_s;
+  double busy_s;            /* first submit -> last completion */
+} fcs_stats;
+
+/* Start a server (allocates the arena, staging and streams once). */
+int fcs_server_create(const fcs_server_config *cfg, fcs_server **server);
+/* Stop admitting, finish in-flight rounds, cancel queued requests, free. */
+int fcs_server_destroy(fcs_server *server);
+/* Queue a request; never blocks on the GPU.  FCS_ENOMEM_BUDGET when it could
+ * never fit the arena or staging; FCS_EINVAL for bad fields or an unknown or
+ * released sketch_id. */
+int fcs_server_submit(fcs_server *server, const fcs_request *req, int64_t *ticket);
+/* Non-blocking state of a request. */
+int fcs_server_poll(fcs_server *server, int64_t ticket, fcs_result *res);
+/* Wait at most timeout_s seconds; FCS_ETIMEOUT if still unfinished. */
+int fcs_server_wait(fcs_server *server, int64_t ticket, double timeout_s, fcs_result *res);
+/* Cancel a request that has not been admitted yet (else FCS_EINVAL). */
+int fcs_server_cancel(fcs_server *server, int64_t ticket);
+/* Drop a resident sketch once no queued or running request uses it. */
+int fcs_server_release(fcs_server *server, int64_t sketch_id);
+/* Counters and latency percentiles of completed requests. */
+int fcs_server_stats(fcs_server *server, fcs_stats *out);
+int fcs_server_reset_stats(fcs_server *server);
+
+/*
  * fcs_contract -- sketched contractions of Sec. 4.1, one per batch item b:
  *  kind FCS_CONTRACT_ALL, eq. (T_uvw):
  *      raw[b][d] = < FCS_d(T), FCS_d(v_1 o ... o v_N) >, evaluated as

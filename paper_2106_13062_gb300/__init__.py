@@ -95,6 +95,18 @@ def lib() -> C.CDLL:
                                                   C.c_int]),
                 "fcs_batch_autotune": (C.c_int, [vp, C.c_int, C.POINTER(CpProblem),
                                                  C.POINTER(C.c_int)]),
+                "fcs_server_create": (C.c_int, [C.POINTER(ServerConfig),
+                                                C.POINTER(C.c_void_p)]),
+                "fcs_server_destroy": (C.c_int, [vp]),
+                "fcs_server_submit": (C.c_int, [vp, C.POINTER(Request),
+                                                C.POINTER(C.c_int64)]),
+                "fcs_server_poll": (C.c_int, [vp, C.c_int64, C.POINTER(Result)]),
+                "fcs_server_wait": (C.c_int, [vp, C.c_int64, C.c_double,
+                                              C.POINTER(Result)]),
+                "fcs_server_cancel": (C.c_int, [vp, C.c_int64]),
+                "fcs_server_release": (C.c_int, [vp, C.c_int64]),
+                "fcs_server_stats": (C.c_int, [vp, C.POINTER(Stats)]),
+                "fcs_server_reset_stats": (C.c_int, [vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -114,6 +126,44 @@ class CpProblem(C.Structure):
                 ("ldh", C.c_int64), ("out", C.c_void_p)]
 
 
+FCS_REQ_CP = 0
+FCS_REQ_CONTRACT = 1
+
+
+class ServerConfig(C.Structure):
+    """Mirror of `fcs_server_config`."""
+    _fields_ = [("device", C.c_int), ("streams", C.c_int), ("max_inflight", C.c_int),
+                ("max_batch", C.c_int), ("arena_bytes", C.c_size_t),
+                ("staging_bytes", C.c_size_t), ("workspace_bytes", C.c_size_t)]
+
+
+class Request(C.Structure):
+    """Mirror of `fcs_request`."""
+    _fields_ = [("kind", C.c_int), ("N", C.c_int), ("I", C.c_int64 * 8),
+                ("J", C.c_int32 * 8), ("D", C.c_int), ("R", C.c_int64),
+                ("seed", C.c_uint64), ("host_U", C.c_void_p * 8),
+                ("host_lambda", C.c_void_p), ("host_out", C.c_void_p),
+                ("keep_resident", C.c_int), ("sketch_id", C.c_int64),
+                ("contract_kind", C.c_int), ("free_mode", C.c_int), ("B", C.c_int64),
+                ("host_vecs", C.c_void_p * 8), ("host_result", C.c_void_p)]
+
+
+class Result(C.Structure):
+    """Mirror of `fcs_result`."""
+    _fields_ = [("ticket", C.c_int64), ("state", C.c_int), ("status", C.c_int),
+                ("sketch_id", C.c_int64), ("latency_s", C.c_double)]
+
+
+class Stats(C.Structure):
+    """Mirror of `fcs_stats`."""
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64),
+                ("failed", C.c_int64), ("cancelled", C.c_int64),
+                ("rounds", C.c_int64), ("sketches", C.c_int64),
+                ("max_inflight_seen", C.c_int64), ("arena_used", C.c_size_t),
+                ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double),
+                ("mean_latency_s", C.c_double), ("busy_s", C.c_double)]
+
+
 def exported_symbols():
     """Names of the C entry points this binding expects libfcs.so to export."""
     return ["fcs_version", "fcs_create", "fcs_destroy", "fcs_set_stream",
@@ -121,7 +171,10 @@ def exported_symbols():
             "fcs_sketch_dense", "fcs_sketch_cp", "fcs_sketch_cp_noalloc",
             "fcs_contract", "fcs_recover", "fcs_sketch_outer",
             "fcs_batch_plan_create", "fcs_batch_plan_launch",
-            "fcs_batch_plan_destroy", "fcs_batch_sketch_cp", "fcs_batch_autotune"]
+            "fcs_batch_plan_destroy", "fcs_batch_sketch_cp", "fcs_batch_autotune",
+            "fcs_server_create", "fcs_server_destroy", "fcs_server_submit",
+            "fcs_server_poll", "fcs_server_wait", "fcs_server_cancel",
+            "fcs_server_release", "fcs_server_stats", "fcs_server_reset_stats"]
 
 
 # ------------------------------------------------------------------ helpers
@@ -506,3 +559,143 @@ def fcs_batch_plan_launch(ctx: Context, plan: BatchPlan):
 def fcs_batch_plan_destroy(plan: BatchPlan):
     """C-ABI-named alias of plan.close()."""
     plan.close()
+
+
+# ------------------------------------------------------------------ serving
+class FcsServer:
+    """The request server (fcs_server_*).  Requests carry host numpy buffers;
+    this object keeps them alive until the request finishes."""
+
+    def __init__(self, device: int = 0, streams: int = 4, max_inflight: int = 64,
+                 max_batch: int = 32, arena_bytes: int = 2 << 30,
+                 staging_bytes: int = 512 << 20, workspace_bytes: int | None = None):
+        cfg = ServerConfig(device, streams, max_inflight, max_batch, arena_bytes,
+                           staging_bytes,
+                           C.c_size_t(-1).value if workspace_bytes is None else workspace_bytes)
+        h = C.c_void_p()
+        rc = lib().fcs_server_create(C.byref(cfg), C.byref(h))
+        if rc != FCS_OK:
+            raise FcsError(rc, "fcs_server_create failed")
+        self._h = h
+        self._keep = {}
+
+    def _submit(self, req, keep):
+        t = C.c_int64()
+        rc = lib().fcs_server_submit(self._h, C.byref(req), C.byref(t))
+        if rc != FCS_OK:
+            raise FcsError(rc, "fcs_server_submit rejected the request")
+        self._keep[t.value] = keep
+        return t.value
+
+    def submit_cp(self, U, lam, J, D: int, seed: int, out=None, keep_resident=False):
+        """Sketch the CP tensor [[lam; U_1..U_N]] (host float32 arrays) into
+        `out` ([D, Jt] float32, host) and/or keep it resident."""
+        import numpy as np
+        U = [np.ascontiguousarray(u, dtype=np.float32) for u in U]
+        lam = None if lam is None else np.ascontiguousarray(lam, dtype=np.float32)
+        r = Request()
+        r.kind, r.N, r.D, r.R, r.seed = FCS_REQ_CP, len(U), D, U[0].shape[1], seed
+        for k, u in enumerate(U):
+            r.I[k], r.J[k] = u.shape[0], int(J[k])
+            r.host_U[k] = u.ctypes.data
+        r.host_lambda = None if lam is None else lam.ctypes.data
+        r.host_out = None if out is None else out.ctypes.data
+        r.keep_resident = 1 if keep_resident else 0
+        return self._submit(r, (U, lam, out))
+
+    def submit_contract(self, sketch_id: int, I, J, kind: int, vecs, result,
+                        free_mode: int = 0):
+        """Contract host vectors ([B, I_n] float32) with resident sketch
+        `sketch_id`; the median over sketches lands in `result`."""
+        import numpy as np
+        vv = [None if v is None else np.ascontiguousarray(v, dtype=np.float32) for v in vecs]
+        r = Request()
+        r.kind, r.N, r.sketch_id = FCS_REQ_CONTRACT, len(I), sketch_id
+        r.contract_kind, r.free_mode = kind, free_mode
+        r.B = next(v for v in vv if v is not None).shape[0]
+        for k in range(len(I)):
+            r.I[k], r.J[k] = int(I[k]), int(J[k])
+            r.host_vecs[k] = None if vv[k] is None else vv[k].ctypes.data
+        r.host_result = result.ctypes.data
+        return self._submit(r, (vv, result))
+
+    def poll(self, ticket: int) -> Result:
+        res = Result()
+        lib().fcs_server_poll(self._h, ticket, C.byref(res))
+        if res.state >= 2:
+            self._keep.pop(ticket, None)
+        return res
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> Result:
+        res = Result()
+        rc = lib().fcs_server_wait(self._h, ticket, timeout_s, C.byref(res))
+        if rc not in (FCS_OK, FCS_ETIMEOUT):
+            raise FcsError(rc, "fcs_server_wait failed")
+        if res.state >= 2:
+            self._keep.pop(ticket, None)
+        return res
+
+    def cancel(self, ticket: int) -> int:
+        return lib().fcs_server_cancel(self._h, ticket)
+
+    def release(self, sketch_id: int) -> int:
+        return lib().fcs_server_release(self._h, sketch_id)
+
+    def stats(self) -> Stats:
+        st = Stats()
+        lib().fcs_server_stats(self._h, C.byref(st))
+        return st
+
+    def reset_stats(self):
+        lib().fcs_server_reset_stats(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().fcs_server_destroy(self._h)
+            self._h = C.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fcs_server_create(**kw) -> FcsServer:
+    """C-ABI-named alias of FcsServer(**kw)."""
+    return FcsServer(**kw)
+
+
+def fcs_server_destroy(server: FcsServer):
+    server.close()
+
+
+def fcs_server_submit(server: FcsServer, kind: int, **kw) -> int:
+    """Submit through the C entry point: kind FCS_REQ_CP takes the keywords of
+    FcsServer.submit_cp, FCS_REQ_CONTRACT those of submit_contract."""
+    return server.submit_cp(**kw) if kind == FCS_REQ_CP else server.submit_contract(**kw)
+
+
+def fcs_server_poll(server: FcsServer, ticket: int) -> Result:
+    return server.poll(ticket)
+
+
+def fcs_server_wait(server: FcsServer, ticket: int, timeout_s: float = 60.0) -> Result:
+    return server.wait(ticket, timeout_s)
+
+
+def fcs_server_cancel(server: FcsServer, ticket: int) -> int:
+    return server.cancel(ticket)
+
+
+def fcs_server_release(server: FcsServer, sketch_id: int) -> int:
+    return server.release(sketch_id)
+
+
+def fcs_server_stats(server: FcsServer) -> Stats:
+    return server.stats()
+
+
+def fcs_server_reset_stats(server: FcsServer):
+    server.reset_stats()

@@ -30,6 +30,7 @@
 #include <map>
 #include <vector>
 
+#include "fcs_batch_internal.cuh"
 #include "fcs_fft.cuh"
 
 struct fcs_batch_state {
@@ -41,11 +42,7 @@ struct fcs_batch_plan {
   int device = 0;
   void *dev = nullptr;             // descriptors, items, tasks, tickets, G, UT
   size_t bytes = 0;
-  size_t clear_off = 0, clear_bytes = 0;
-  int nitems = 0, ntasks = 0, grid = 0;
-  int64_t tiles = 0;
-  size_t smem = 0;
-  size_t items_off = 0, tasks_off = 0;
+  fcs::BatchBuild build{};
   fcs_ctx *owner = nullptr;
 };
 
@@ -401,10 +398,14 @@ int default_grain(const fcs_ctx *ctx, int nprob, const fcs_cp_problem *q) {
   return int(std::min<int64_t>(grain, rmax));
 }
 
-// Build a plan: validate, cut items, lay out and upload the descriptors.
-int plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain,
-                fcs_batch_plan **out) {
-  *out = nullptr;
+}  // namespace
+
+// Lay a batch out at device address `base` (NULL: sizes only).  The device
+// image starts with the descriptors (probs | items | tasks), `desc_bytes`
+// long, whose host copy goes to *host_desc; then the cleared region (queue
+// + tickets | spectrum accumulators) and the transposed factors.
+int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, char *base,
+                std::vector<char> *host_desc, BatchBuild *out) {
   std::vector<HostProb> hp(nprob);
   for (int k = 0; k < nprob; ++k) {
     int rc = check_problem(ctx, k, q[k], &hp[k]);
@@ -438,27 +439,22 @@ int plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain,
   const size_t b_tasks = up256(sizeof(TransposeTask) * ntask);
   const size_t b_tick = up256(sizeof(unsigned) * (1 + t_count));
   const size_t b_ut = up256(sizeof(float) * ut_len);
-  const size_t total = b_probs + b_items + b_tasks + b_tick + g_bytes + b_ut;
-  if (ctx->ws_bytes + ctx->plan_bytes + total > ctx->budget)
-    return set_error(ctx, FCS_ENOMEM_BUDGET,
-                     "batch plan of %zu bytes exceeds the context budget of %zu", total,
-                     ctx->budget);
-  fcs_batch_plan *plan = new (std::nothrow) fcs_batch_plan();
-  if (!plan) return set_error(ctx, FCS_ENOMEM_BUDGET, "out of host memory");
-  cudaError_t e = cudaMalloc(&plan->dev, total);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    delete plan;
-    return check_cuda(ctx, e, "cudaMalloc(batch plan)");
+  BatchBuild bb{};
+  bb.total = b_probs + b_items + b_tasks + b_tick + g_bytes + b_ut;
+  bb.desc_bytes = b_probs + b_items + b_tasks;
+  bb.items_off = b_probs;
+  bb.tasks_off = b_probs + b_items;
+  bb.clear_off = b_probs + b_items + b_tasks;
+  bb.clear_bytes = b_tick + g_bytes;
+  bb.nitems = int(items.size());
+  bb.ntasks = ntask;
+  if (!base) {
+    *out = bb;
+    return FCS_OK;
   }
-  plan->bytes = total;
-  plan->device = ctx->device;
-  plan->owner = ctx;
-  char *base = static_cast<char *>(plan->dev);
-  unsigned *d_queue = reinterpret_cast<unsigned *>(base + b_probs + b_items + b_tasks);
-  char *g_base = base + b_probs + b_items + b_tasks + b_tick;
+  unsigned *d_queue = reinterpret_cast<unsigned *>(base + bb.clear_off);
+  char *g_base = base + bb.clear_off + b_tick;
   float *ut_base = reinterpret_cast<float *>(g_base + g_bytes);
-
   std::vector<TransposeTask> tasks;
   size_t goff = 0, toff = 1, uoff = 0, smem = 0;
   int64_t tiles = 0;
@@ -502,63 +498,91 @@ int plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain,
     uoff += size_t(local);
     smem = std::max(smem, batch_smem_bytes(P.L, P.sb));
   }
-  if (tiles > 0x7fffffffLL) {
-    cudaFree(plan->dev);
-    delete plan;
-    return set_error(ctx, FCS_EUNSUPPORTED, "batch too large");
-  }
-  std::vector<char> hb(b_probs + b_items + b_tasks, 0);
-  memcpy(hb.data(), probs.data(), sizeof(BatchProb) * nprob);
-  memcpy(hb.data() + b_probs, items.data(), sizeof(int4) * items.size());
-  memcpy(hb.data() + b_probs + b_items, tasks.data(), sizeof(TransposeTask) * tasks.size());
-  e = cudaMemcpy(base, hb.data(), hb.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    cudaFree(plan->dev);
-    delete plan;
-    return check_cuda(ctx, e, "cudaMemcpy(batch descriptors)");
-  }
+  if (tiles > 0x7fffffffLL) return set_error(ctx, FCS_EUNSUPPORTED, "batch too large");
+  host_desc->assign(bb.desc_bytes, 0);
+  memcpy(host_desc->data(), probs.data(), sizeof(BatchProb) * nprob);
+  memcpy(host_desc->data() + b_probs, items.data(), sizeof(int4) * items.size());
+  memcpy(host_desc->data() + b_probs + b_items, tasks.data(),
+         sizeof(TransposeTask) * tasks.size());
   if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(batch_cp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(smem));
-    if (e != cudaSuccess) {
-      cudaFree(plan->dev);
-      delete plan;
-      return check_cuda(ctx, e, "cudaFuncSetAttribute(batch)");
-    }
+    cudaError_t e = cudaFuncSetAttribute(batch_cp_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(batch)");
   }
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_cp_kernel, kBatchNT, smem);
   if (per_sm < 1) per_sm = 1;
-  plan->nitems = int(items.size());
-  plan->ntasks = int(tasks.size());
-  plan->tiles = tiles;
-  plan->smem = smem;
-  plan->grid = std::max(1, std::min(plan->nitems, ctx->sm_count * per_sm));
-  plan->items_off = b_probs;
-  plan->tasks_off = b_probs + b_items;
-  plan->clear_off = b_probs + b_items + b_tasks;
-  plan->clear_bytes = b_tick + g_bytes;
-  ctx->plan_bytes += total;
+  bb.tiles = tiles;
+  bb.smem = smem;
+  bb.grid = std::max(1, std::min(bb.nitems, ctx->sm_count * per_sm));
+  *out = bb;
+  return FCS_OK;
+}
+
+// Device work of one batch on ctx->stream (descriptors already in place).
+int batch_issue(fcs_ctx *ctx, char *base, const BatchBuild &b) {
+  int rc = check_cuda(ctx, cudaMemsetAsync(base + b.clear_off, 0, b.clear_bytes, ctx->stream),
+                      "cudaMemsetAsync(batch accumulators)");
+  if (rc) return rc;
+  batch_transpose_kernel<<<unsigned(b.tiles), dim3(32, 8), 0, ctx->stream>>>(
+      reinterpret_cast<const TransposeTask *>(base + b.tasks_off), b.ntasks);
+  rc = check_cuda(ctx, cudaGetLastError(), "batch_transpose_kernel");
+  if (rc) return rc;
+  batch_cp_kernel<<<b.grid, kBatchNT, b.smem, ctx->stream>>>(
+      reinterpret_cast<const BatchProb *>(base),
+      reinterpret_cast<const int4 *>(base + b.items_off), b.nitems,
+      reinterpret_cast<unsigned *>(base + b.clear_off), ctx->twiddle);
+  return check_cuda(ctx, cudaGetLastError(), "batch_cp_kernel");
+}
+
+int batch_default_grain(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q) {
+  return default_grain(ctx, nprob, q);
+}
+
+namespace {
+
+// Build a plan: lay the batch out in plan-owned device memory and upload the
+// descriptors.
+int plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain,
+                fcs_batch_plan **out) {
+  *out = nullptr;
+  BatchBuild bb{};
+  std::vector<char> desc;
+  int rc = batch_build(ctx, nprob, q, grain, nullptr, &desc, &bb);
+  if (rc) return rc;
+  if (ctx->ws_bytes + ctx->plan_bytes + bb.total > ctx->budget)
+    return set_error(ctx, FCS_ENOMEM_BUDGET,
+                     "batch plan of %zu bytes exceeds the context budget of %zu", bb.total,
+                     ctx->budget);
+  fcs_batch_plan *plan = new (std::nothrow) fcs_batch_plan();
+  if (!plan) return set_error(ctx, FCS_ENOMEM_BUDGET, "out of host memory");
+  cudaError_t e = cudaMalloc(&plan->dev, bb.total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete plan;
+    return check_cuda(ctx, e, "cudaMalloc(batch plan)");
+  }
+  rc = batch_build(ctx, nprob, q, grain, static_cast<char *>(plan->dev), &desc, &bb);
+  if (rc == FCS_OK)
+    rc = check_cuda(ctx, cudaMemcpy(plan->dev, desc.data(), desc.size(), cudaMemcpyHostToDevice),
+                    "cudaMemcpy(batch descriptors)");
+  if (rc) {
+    cudaFree(plan->dev);
+    delete plan;
+    return rc;
+  }
+  plan->bytes = bb.total;
+  plan->device = ctx->device;
+  plan->owner = ctx;
+  plan->build = bb;
+  ctx->plan_bytes += bb.total;
   *out = plan;
   return FCS_OK;
 }
 
 // Device work only: capturable into a CUDA graph.
 int plan_launch(fcs_ctx *ctx, const fcs_batch_plan *plan) {
-  char *base = static_cast<char *>(plan->dev);
-  int rc = check_cuda(ctx, cudaMemsetAsync(base + plan->clear_off, 0, plan->clear_bytes,
-                                           ctx->stream),
-                      "cudaMemsetAsync(batch accumulators)");
-  if (rc) return rc;
-  batch_transpose_kernel<<<unsigned(plan->tiles), dim3(32, 8), 0, ctx->stream>>>(
-      reinterpret_cast<const TransposeTask *>(base + plan->tasks_off), plan->ntasks);
-  rc = check_cuda(ctx, cudaGetLastError(), "batch_transpose_kernel");
-  if (rc) return rc;
-  batch_cp_kernel<<<plan->grid, kBatchNT, plan->smem, ctx->stream>>>(
-      reinterpret_cast<const BatchProb *>(base),
-      reinterpret_cast<const int4 *>(base + plan->items_off), plan->nitems,
-      reinterpret_cast<unsigned *>(base + plan->clear_off), ctx->twiddle);
-  return check_cuda(ctx, cudaGetLastError(), "batch_cp_kernel");
+  return batch_issue(ctx, static_cast<char *>(plan->dev), plan->build);
 }
 
 void plan_free(fcs_batch_plan *plan) {
