@@ -664,13 +664,201 @@ WORKLOADS = {"cp": CpWorkload, "dense": DenseWorkload, "kron": KronWorkload,
              "batch": BatchWorkload}
 
 
+# ================================================================== serving
+def run_serve(args, rank, world, local_rank):
+    """Serving workload: 10,000 requests with Poisson arrivals, half CP-route
+    sketches (order 3-4, I_n log-U[50,2000], rank log-U[1,256], J_n
+    log-U[256,8192] with Jt <= 16384, D U{1..10}; 96 shape templates), half
+    contractions (T(u,u,u) : T(I,u,u) = 1 : 1, 1-16 vectors) against 16
+    resident sketches.  The offered rate is 0.8 x the capacity of the plain
+    path (one request at a time: copy in, hashes, one launch, copy out,
+    synchronise), measured first.  Both paths see the same arrival
+    schedule; the server's capacity is also measured at saturation."""
+    import threading
+    import torch
+    import paper_2106_13062_gb300 as fcs
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    g = np.random.default_rng(7)
+    nreq = args.requests
+    templates = []
+    for k, (I, J, R, D) in enumerate(mixed_cp_shapes(70, 96)):
+        U, lam = synth.cp_factors(7000 + k, I, R)
+        templates.append((I, J, R, D, U, lam))
+    res_shapes = []
+    for k in range(16):
+        I = [int(g.integers(50, 500))] * 3
+        J = [int(g.integers(256, 2000))] * 3
+        U, lam = synth.cp_factors(8000 + k, I, 8)
+        res_shapes.append((I, J, 8, 5, U, lam, 9000 + k))
+    reqs = []
+    for i in range(nreq):
+        if g.random() < 0.5:
+            reqs.append(("cp", int(g.integers(0, len(templates))), 1000 + i))
+        else:
+            k = int(g.integers(0, len(res_shapes)))
+            kind = fcs.FCS_CONTRACT_ALL if g.random() < 0.5 else fcs.FCS_CONTRACT_FREE
+            B = int(g.integers(1, 17))
+            vec = synth.unit_vectors(20000 + i, B, res_shapes[k][0][0])
+            reqs.append(("ct", k, kind, vec))
+
+    # ---- plain path: one request per launch, synchronised
+    ctx = fcs.Context(local_rank)
+    dU = [[torch.from_numpy(u).to(dev) for u in t[4]] for t in templates]
+    hU = [[torch.from_numpy(u).pin_memory() for u in t[4]] for t in templates]
+    dlam = [torch.from_numpy(t[5]).to(dev) for t in templates]
+    hlam = [torch.from_numpy(t[5]).pin_memory() for t in templates]
+    douts = [torch.empty((t[3], jt_of(t[1])), device=dev) for t in templates]
+    houts = [torch.empty((t[3], jt_of(t[1]))).pin_memory() for t in templates]
+    resident = []
+    for I, J, R, D, U, lam, seed in res_shapes:
+        h, s_ = fcs.fcs_make_hashes(ctx, seed, I, J, D)
+        sk = fcs.fcs_sketch_cp(ctx, [torch.from_numpy(u).to(dev) for u in U],
+                               torch.from_numpy(lam).to(dev), J, h, s_)
+        resident.append((I, J, h, s_, sk))
+    torch.cuda.synchronize()
+
+    def plain(r):
+        if r[0] == "cp":
+            k, seed = r[1], r[2]
+            I, J, R, D, _, _ = templates[k]
+            for d_, h_ in zip(dU[k], hU[k]):
+                d_.copy_(h_, non_blocking=True)
+            dlam[k].copy_(hlam[k], non_blocking=True)
+            h, s_ = fcs.fcs_make_hashes(ctx, seed, I, J, D)
+            fcs.fcs_sketch_cp(ctx, dU[k], dlam[k], J, h, s_, out=douts[k])
+            houts[k].copy_(douts[k], non_blocking=True)
+        else:
+            _, k, kind, vec = r
+            I, J, h, s_, sk = resident[k]
+            v = torch.from_numpy(vec).to(dev, non_blocking=True)
+            vv = [None if (kind == fcs.FCS_CONTRACT_FREE and m == 0) else v for m in range(3)]
+            out = fcs.fcs_contract(ctx, kind, sk, vv, I, J, h, s_, free_mode=0)
+            out.cpu()
+        torch.cuda.synchronize()
+
+    for r in reqs[:20]:
+        plain(r)
+    t0 = time.perf_counter()
+    ncap = min(400, nreq)
+    for r in reqs[:ncap]:
+        plain(r)
+    mu = ncap / (time.perf_counter() - t0)              # requests/s
+    lam_rate = 0.8 * mu
+    arrivals = np.cumsum(g.exponential(1.0 / lam_rate, size=nreq))
+    sk_per_req = [templates[r[1]][3] if r[0] == "cp" else 0 for r in reqs]
+
+    # plain path under the arrival schedule
+    lat_plain = np.empty(nreq)
+    start = time.perf_counter()
+    for i, r in enumerate(reqs):
+        while time.perf_counter() - start < arrivals[i]:
+            pass
+        plain(r)
+        lat_plain[i] = time.perf_counter() - start - arrivals[i]
+    plain_wall = time.perf_counter() - start
+
+    # ---- served path under the same schedule
+    srv = fcs.FcsServer(device=local_rank, streams=4, max_inflight=128, max_batch=48,
+                        arena_bytes=6 << 30, staging_bytes=2 << 30)
+    sids = []
+    for I, J, R, D, U, lam, seed in res_shapes:
+        t = srv.submit_cp(U, lam, J, D, seed=seed, keep_resident=True)
+        sids.append(srv.wait(t, 120.0).sketch_id)
+
+    def submit(r, out_store, idx):
+        if r[0] == "cp":
+            I, J, R, D, U, lam = templates[r[1]]
+            out = np.empty((D, jt_of(J)), dtype=np.float32)
+            out_store[idx] = out
+            return srv.submit_cp(U, lam, J, D, seed=r[2], out=out)
+        _, k, kind, vec = r
+        I, J = res_shapes[k][0], res_shapes[k][1]
+        out = np.empty((vec.shape[0],) if kind == fcs.FCS_CONTRACT_ALL
+                       else (vec.shape[0], I[0]), dtype=np.float32)
+        out_store[idx] = out
+        vv = [None if (kind == fcs.FCS_CONTRACT_FREE and m == 0) else vec for m in range(3)]
+        return srv.submit_contract(sids[k], I, J, kind, vv, out)
+
+    def served_run(sched):
+        srv.reset_stats()
+        tickets = [None] * nreq
+        outs = [None] * nreq
+
+        def producer():
+            st0 = time.perf_counter()
+            for i, r in enumerate(reqs):
+                if sched is not None:
+                    while time.perf_counter() - st0 < sched[i]:
+                        time.sleep(0)
+                tickets[i] = submit(r, outs, i)
+        th = threading.Thread(target=producer)
+        t_start = time.perf_counter()
+        th.start()
+        lat = np.empty(nreq)
+        for i in range(nreq):
+            while tickets[i] is None:
+                time.sleep(0)
+            res = srv.wait(tickets[i], 600.0)
+            if res.state != 2:
+                raise RuntimeError(f"request {i} ended in state {res.state}")
+            lat[i] = res.latency_s
+        th.join()
+        wall = time.perf_counter() - t_start
+        st = srv.stats()
+        return lat, wall, st
+
+    lat_srv, srv_wall, st_srv = served_run(arrivals)
+    lat_sat, sat_wall, st_sat = served_run(None)
+    srv.close()
+    ctx.close()
+    sk_total = float(sum(sk_per_req))
+    plain_cap_sk = mu * sk_total / nreq
+    res = {
+        "impl": "fcs",
+        "metric": "served sketch requests: sketches/s at saturation, p50/p99 latency at 0.8x plain capacity",
+        "value": sk_total / sat_wall, "unit": "sketches/s", "n_gpus": world,
+        "steps": nreq, "warmup": 20, "ms_per_step": 1e3 * sat_wall / nreq,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "serve_10k_poisson_mixed", "requests": nreq,
+                   "mix": "50% CP sketch (96 templates, order 3-4, I log-U[50,2000], R log-U[1,256], J log-U[256,8192], Jt<=16384, D U{1..10}); 50% contractions UUU:IUU 1:1, B U{1..16}, 16 resident sketches",
+                   "arrivals": "Poisson, rate 0.8 x measured plain capacity", "seed": 7,
+                   "server": "4 streams, 128 slots, 48 CP per round"},
+        "serving": {
+            "offered_rate_req_s": lam_rate,
+            "plain_capacity_req_s": mu, "plain_capacity_sketches_s": plain_cap_sk,
+            "served_capacity_req_s": nreq / sat_wall,
+            "served_capacity_sketches_s": sk_total / sat_wall,
+            "capacity_ratio_served_over_plain": (nreq / sat_wall) / mu,
+            "plain_p50_s": float(np.percentile(lat_plain, 50)),
+            "plain_p99_s": float(np.percentile(lat_plain, 99)),
+            "served_p50_s": float(np.percentile(lat_srv, 50)),
+            "served_p99_s": float(np.percentile(lat_srv, 99)),
+            "plain_wall_s": plain_wall, "served_wall_s": srv_wall,
+            "served_rounds": st_srv.rounds, "served_max_inflight": st_srv.max_inflight_seen,
+            "saturation_rounds": st_sat.rounds,
+            "saturation_p50_s": float(np.percentile(lat_sat, 50)),
+            "saturation_p99_s": float(np.percentile(lat_sat, 99)),
+        },
+        # saturation run: per round a batched transpose + persistent kernel,
+        # per CP request a hash kernel, per contraction spectrum + contract +
+        # median kernels
+        "gpu_launches": int(2 * st_sat.rounds + sum(1 for r in reqs if r[0] == "cp")
+                            + 3 * sum(1 for r in reqs if r[0] == "ct")),
+    }
+    return res
+
+
 # ================================================================== arms
 def run_reference(args, rank, world):
     """The FP64 oracle as the reference arm, on the host cores, rank 0 only."""
     if rank != 0:
         return None
-    w = WORKLOADS[args.workload]()
-    if not hasattr(w, "reference_step"):
+    w = WORKLOADS[args.workload]() if args.workload in WORKLOADS else None
+    if w is None or not hasattr(w, "reference_step"):
         return {"impl": "reference", "unavailable":
                 f"reference arm only defined for the default workload (cp), not {args.workload}"}
     w.reference_setup()
@@ -798,7 +986,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["fcs", "reference"], default="fcs")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cp")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve"], default="cp")
+    ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -817,7 +1006,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    res = run_fcs(args, rank, world, local_rank)
+    res = (run_serve if args.workload == "serve" else run_fcs)(args, rank, world, local_rank)
     if res is not None:
         print(json.dumps(res), flush=True)
     if world > 1:
