@@ -14,7 +14,7 @@
 // (batch item, sketch) that builds each needed Count Sketch in shared memory,
 // transforms it and folds it into the per-thread spectrum product, then either
 // reduces the Parseval sum or runs the inverse FFT and gathers; (3) the median.
-#include "fcs_internal.cuh"
+#include "fcs_fft.cuh"
 
 namespace fcs {
 namespace {
@@ -32,82 +32,89 @@ struct ContractArgs {
   float2 *spec;           // [D][M+1]
   float *raw;             // [B][D] or [B][D][I_m]
   float *out;             // [B] or [B][I_m]
+  int sb;                 // compact count-sketch buffer (floats, multiple of 4)
 };
 
-// Half spectrum of each of the D sketches of T, natural order [D][M+1].
+// Half spectrum of each of the D sketches of T, natural order [D][M+1]: the
+// sketch is read into the compact real buffer and transformed by the block
+// real FFT whose last pass leaves the spectrum in registers.
 template <int LOG2M, int NT>
 __global__ void __launch_bounds__(NT) spectrum_kernel(const float *__restrict__ x, int64_t len,
-                                                      int64_t ld, float2 *__restrict__ spec,
+                                                      int64_t ld, int sb,
+                                                      float2 *__restrict__ spec,
                                                       const float2 *__restrict__ tw) {
+  using LPs = LastPass<LOG2M, NT>;
+  using Lay = FftSmem<LOG2M>;
   constexpr int M = 1 << LOG2M;
-  constexpr int HALF = M / 2;
-  constexpr int EP = (HALF + NT - 1) / NT;
-  extern __shared__ __align__(16) float2 buf[];
-  float *bufr = reinterpret_cast<float *>(buf);
-  const int tid = threadIdx.x;
+  constexpr int RL = LPs::RL, EPS = LPs::EPS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2 *B = reinterpret_cast<float2 *>(smem + Lay::kB);
+  float2 *tws = reinterpret_cast<float2 *>(smem + Lay::kTw);
+  float *A = reinterpret_cast<float *>(smem + Lay::kA);
   const float *xd = x + blockIdx.x * ld;
-  for (int e = tid; e < padded_len(M); e += NT) buf[e] = make_float2(0.f, 0.f);
-  __syncthreads();
-  for (int64_t j = tid; j < len; j += NT) bufr[real_off(int(j))] = __ldg(xd + j);
-  __syncthreads();
-  block_fft<LOG2M, NT>(buf, tw);
+  fill_twiddles<LOG2M, NT>(tws, tw);
+  for (int j = threadIdx.x; j < sb; j += NT) A[j] = j < len ? __ldg(xd + j) : 0.f;
+  float2 X[EPS][2][RL];
+  rfft_to_slots<LOG2M, NT>(A, sb, B, tws, tw, X);
   float2 *sd = spec + blockIdx.x * int64_t(M + 1);
 #pragma unroll
-  for (int e = 0; e < EP; ++e) {
-    const int q = tid + e * NT;
-    if (q < HALF) {
-      float2 A, B;
-      unpack_pair<LOG2M>(buf, q, tw, A, B);
-      if (q == 0) {
-        sd[0] = make_float2(A.x, 0.f);
-        sd[M] = make_float2(A.y, 0.f);
-        sd[HALF] = B;
-      } else {
-        sd[q] = A;
-        sd[M - q] = B;
+  for (int e = 0; e < EPS; ++e) {
+    if (LPs::SLOTS % NT != 0 && int(threadIdx.x) + e * NT >= LPs::SLOTS) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int q = last_pass_index<LOG2M, NT>(e, b, r);
+        if (q == 0) {
+          sd[0] = make_float2(X[e][b][r].x, 0.f);
+          sd[M] = make_float2(X[e][b][r].y, 0.f);
+        } else {
+          sd[q] = X[e][b][r];
+        }
       }
-    }
   }
 }
 
 template <int LOG2M, int NT>
 __global__ void __launch_bounds__(NT) contract_kernel(ContractArgs a,
                                                       const float2 *__restrict__ tw) {
+  using LPs = LastPass<LOG2M, NT>;
+  using Lay = FftSmem<LOG2M>;
   constexpr int M = 1 << LOG2M;
-  constexpr int HALF = M / 2;
-  constexpr int EP = (HALF + NT - 1) / NT;
-  extern __shared__ __align__(16) float2 buf[];
-  float *bufr = reinterpret_cast<float *>(buf);
+  constexpr int RL = LPs::RL, EPS = LPs::EPS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2 *B = reinterpret_cast<float2 *>(smem + Lay::kB);
+  float2 *tws = reinterpret_cast<float2 *>(smem + Lay::kTw);
+  float *A = reinterpret_cast<float *>(smem + Lay::kA);
   __shared__ float red[NT / 32];
   const int tid = threadIdx.x;
   const int64_t b = blockIdx.x;
   const int d = blockIdx.y;
   const bool all = a.kind == FCS_CONTRACT_ALL;
+  const int sb = a.sb;
   const float2 *sd = a.spec + d * int64_t(M + 1);
+  fill_twiddles<LOG2M, NT>(tws, tw);
+  for (int e = tid; e < sb / 4; e += NT)
+    reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-  // sketch-of-T spectrum slots for this thread's pairs
-  float2 FA[EP], FB[EP], pA[EP], pB[EP];
+  // spectrum of FCS_d(T) in this thread's slots, and the running product
+  float2 F[EPS][2][RL], p[EPS][2][RL], X[EPS][2][RL];
 #pragma unroll
-  for (int e = 0; e < EP; ++e) {
-    const int q = tid + e * NT;
-    FA[e] = FB[e] = make_float2(0.f, 0.f);
-    if (q < HALF) {
-      if (q == 0) {
-        FA[e] = make_float2(sd[0].x, sd[M].x);
-        FB[e] = sd[HALF];
-      } else {
-        FA[e] = sd[q];
-        FB[e] = sd[M - q];
+  for (int e = 0; e < EPS; ++e)
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const bool live = LPs::SLOTS % NT == 0 || tid + e * NT < LPs::SLOTS;
+        const int q = live ? last_pass_index<LOG2M, NT>(e, bb, r) : 1;
+        F[e][bb][r] = live ? (q == 0 ? make_float2(sd[0].x, sd[M].x) : sd[q])
+                           : make_float2(0.f, 0.f);
+        // multiplicative identity; the q = 0 slot packs two reals
+        p[e][bb][r] = all ? make_float2(1.f, q == 0 ? 1.f : 0.f) : F[e][bb][r];
       }
-    }
-    // multiplicative identity: slot A of pair 0 packs two reals
-    pA[e] = all ? make_float2(1.f, q == 0 ? 1.f : 0.f) : FA[e];
-    pB[e] = all ? make_float2(1.f, 0.f) : FB[e];
-  }
 
   for (int n = 0; n < a.m.N; ++n) {
     if (!all && n == a.free_mode) continue;
-    for (int e = tid; e < padded_len(M); e += NT) buf[e] = make_float2(0.f, 0.f);
     __syncthreads();
     const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
     const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
@@ -115,40 +122,37 @@ __global__ void __launch_bounds__(NT) contract_kernel(ContractArgs a,
     for (int64_t i = tid; i < a.m.I[n]; i += NT) {
       float v = __ldg(vn + i);
       if (__ldg(sn + i) < 0) v = -v;
-      const int p = __ldg(hn + i);
-      if (unsigned(p) < unsigned(2 * M)) atomicAdd(bufr + real_off(p), v);
+      const int hb = __ldg(hn + i);
+      if (unsigned(hb) < unsigned(sb)) atomicAdd(A + hb, v);
     }
-    __syncthreads();
-    block_fft<LOG2M, NT>(buf, tw);
+    rfft_to_slots<LOG2M, NT>(A, sb, B, tws, tw, X);
 #pragma unroll
-    for (int e = 0; e < EP; ++e) {
-      const int q = tid + e * NT;
-      if (q < HALF) {
-        float2 A, Bv;
-        unpack_pair<LOG2M>(buf, q, tw, A, Bv);
-        if (all) {
-          pA[e] = slot_mul(pA[e], A, q == 0);
-          pB[e] = cmul(pB[e], Bv);
-        } else {
-          pA[e] = slot_mulconj(pA[e], A, q == 0);
-          pB[e] = cmulconj(pB[e], Bv);
+    for (int e = 0; e < EPS; ++e)
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const bool packed = bb == 0 && r == 0 && tid + e * NT == 0;
+          p[e][bb][r] = all ? slot_mul(p[e][bb][r], X[e][bb][r], packed)
+                            : slot_mulconj(p[e][bb][r], X[e][bb][r], packed);
         }
-      }
-    }
-    __syncthreads();
   }
 
   if (all) {
-    // sum_{k<P} conj(F_T[k]) Y[k] = F_T[0]Y[0] + F_T[M]Y[M] + 2 sum_{0<k<M} Re(..)
+    // sum_{k<P} conj(F_T[k]) Y[k]: the packed q = 0 slot holds the real bins
+    // 0 and M (weight 1); every other bin q in (0, M) appears twice
     float part = 0.f;
 #pragma unroll
-    for (int e = 0; e < EP; ++e) {
-      const int q = tid + e * NT;
-      if (q < HALF) {
-        const float wa = (q == 0) ? 1.f : 2.f;
-        part += wa * (FA[e].x * pA[e].x + FA[e].y * pA[e].y);
-        part += 2.f * (FB[e].x * pB[e].x + FB[e].y * pB[e].y);
-      }
+    for (int e = 0; e < EPS; ++e) {
+      if (LPs::SLOTS % NT != 0 && tid + e * NT >= LPs::SLOTS) continue;
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const bool packed = bb == 0 && r == 0 && tid + e * NT == 0;
+          const float dot = F[e][bb][r].x * p[e][bb][r].x + F[e][bb][r].y * p[e][bb][r].y;
+          part += packed ? dot : 2.f * dot;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -163,23 +167,20 @@ __global__ void __launch_bounds__(NT) contract_kernel(ContractArgs a,
   }
 
   // FREE: inverse transform of the product, then gather at h_m(i)
-#pragma unroll
-  for (int e = 0; e < EP; ++e) {
-    const int q = tid + e * NT;
-    if (q < HALF) pack_pair_conj<LOG2M>(buf, q, pA[e], pB[e], tw);
-  }
+  slots_to_conj_packed<LOG2M, NT>(B, p, tw);
   __syncthreads();
-  block_fft<LOG2M, NT>(buf, tw);
+  block_fft<LOG2M, NT>(B, tw);
   const int m = a.free_mode;
   const int32_t *hm = a.h + d * a.m.ldh + a.m.off[m];
   const int8_t *sm = a.s + d * a.m.ldh + a.m.off[m];
   const int64_t Im = a.m.I[m];
   float *rawbd = a.raw + (b * a.D + d) * Im;
   const float sc = 1.0f / float(M);
+  const float *bufr = reinterpret_cast<const float *>(B);
   for (int64_t i = tid; i < Im; i += NT) {
-    const int p = __ldg(hm + i);
-    const float v = unsigned(p) < unsigned(2 * M) ? bufr[real_off(p)] : __int_as_float(0x7fc00000);
-    const float z = (p & 1) ? -v * sc : v * sc;
+    const int pz = __ldg(hm + i);
+    const float v = unsigned(pz) < unsigned(2 * M) ? bufr[real_off(pz)] : __int_as_float(0x7fc00000);
+    const float z = (pz & 1) ? -v * sc : v * sc;
     rawbd[i] = __ldg(sm + i) < 0 ? -z : z;
   }
 }
@@ -202,20 +203,21 @@ __global__ void median_kernel(const float *__restrict__ raw, int64_t B, int64_t 
 template <int LOG2M>
 int launch_contract(fcs_ctx *ctx, ContractArgs &a, int64_t Jt) {
   constexpr int NT = fft_threads(LOG2M);
-  const size_t smem = sizeof(float2) * padded_len(1 << LOG2M);
+  const int sb_spec = int((Jt + 3) / 4 * 4);
+  const size_t smem1 = FftSmem<LOG2M>::bytes(sb_spec);
+  const size_t smem2 = FftSmem<LOG2M>::bytes(a.sb);
   auto k1 = spectrum_kernel<LOG2M, NT>;
   auto k2 = contract_kernel<LOG2M, NT>;
-  if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(contract)");
-  }
-  k1<<<a.D, NT, smem, ctx->stream>>>(a.fcsT, Jt, Jt, a.spec, ctx->twiddle);
+  cudaError_t e = cudaSuccess;
+  if (smem1 > 48 * 1024)
+    e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem1));
+  if (e == cudaSuccess && smem2 > 48 * 1024)
+    e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem2));
+  if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(contract)");
+  k1<<<a.D, NT, smem1, ctx->stream>>>(a.fcsT, Jt, Jt, sb_spec, a.spec, ctx->twiddle);
   int rc = check_cuda(ctx, cudaGetLastError(), "spectrum_kernel");
   if (rc) return rc;
-  k2<<<dim3(unsigned(a.B), unsigned(a.D)), NT, smem, ctx->stream>>>(a, ctx->twiddle);
+  k2<<<dim3(unsigned(a.B), unsigned(a.D)), NT, smem2, ctx->stream>>>(a, ctx->twiddle);
   return check_cuda(ctx, cudaGetLastError(), "contract_kernel");
 }
 
@@ -284,6 +286,11 @@ extern "C" int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
   a.h = h;
   a.s = s;
   a.out = out_median;
+  {
+    int64_t jmax = 0;
+    for (int n = 0; n < N; ++n) jmax = host_J[n] > jmax ? host_J[n] : jmax;
+    a.sb = int((jmax + 3) / 4 * 4);
+  }
   const int64_t width = kind == FCS_CONTRACT_ALL ? 1 : host_I[free_mode];
   const size_t sbytes = (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
   const size_t rbytes = out_raw ? 0 : sizeof(float) * size_t(B) * D * size_t(width);

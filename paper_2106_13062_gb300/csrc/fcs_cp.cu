@@ -41,6 +41,39 @@ struct CpArgs {
   int sb;                // scatter buffer length (floats): max J_n rounded up to 4
 };
 
+// All modes in one launch: mode n = blockIdx.z.
+struct TransposeArgs {
+  const float *U[kMaxN];
+  int64_t I[kMaxN], ld[kMaxN], ut_off[kMaxN];
+  int64_t R;
+  const float *lambda;
+  float *UT;
+};
+
+// UT[n][r][i] = U_n[i*ld + r] (times lambda_r for n = 0).
+__global__ void transpose_all_kernel(TransposeArgs t) {
+  __shared__ float tile[32][33];
+  const int n = blockIdx.z;
+  const int64_t I = t.I[n], R = t.R, ld = t.ld[n];
+  const float *U = t.U[n];
+  const float *lambda = n == 0 ? t.lambda : nullptr;
+  float *UT = t.UT + t.ut_off[n];
+  const int64_t i0 = blockIdx.x * 32ll, r0 = blockIdx.y * 32ll;
+  if (i0 >= I) return;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t i = i0 + k, r = r0 + threadIdx.x;
+    if (i < I && r < R) tile[k][threadIdx.x] = U[i * ld + r];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + k, i = i0 + threadIdx.x;
+    if (i < I && r < R) {
+      const float lam = lambda ? __ldg(lambda + r) : 1.f;
+      UT[r * I + i] = tile[threadIdx.x][k] * lam;
+    }
+  }
+}
+
 // UT[n][r][i] = U_n[i*ld + r] (times lambda_r for n = 0).
 __global__ void transpose_factors_kernel(const float *__restrict__ U, int64_t I, int64_t R,
                                          int64_t ld, const float *__restrict__ lambda,
@@ -309,12 +342,22 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
   rc = check_cuda(ctx, cudaMemsetAsync(ws, 0, gbytes + cbytes, ctx->stream),
                   "cudaMemsetAsync(cp workspace)");
   if (rc) return rc;
-  for (int n = 0; n < N; ++n) {
-    dim3 grid(unsigned((host_I[n] + 31) / 32), unsigned((R + 31) / 32));
-    if (grid.y > 65535) return set_error(ctx, FCS_EUNSUPPORTED, "rank too large");
-    transpose_factors_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(
-        host_U[n], host_I[n], R, host_ldU[n], n == 0 ? lambda : nullptr, UT + a.ut_off[n]);
-    rc = check_cuda(ctx, cudaGetLastError(), "transpose_factors_kernel");
+  {
+    TransposeArgs t{};
+    for (int n = 0; n < N; ++n) {
+      t.U[n] = host_U[n];
+      t.I[n] = host_I[n];
+      t.ld[n] = host_ldU[n];
+      t.ut_off[n] = a.ut_off[n];
+    }
+    t.R = R;
+    t.lambda = lambda;
+    t.UT = UT;
+    dim3 grid(unsigned((Imax + 31) / 32), unsigned((R + 31) / 32), unsigned(N));
+    if (grid.y > 65535 || grid.x > 0x7fffffffu)
+      return set_error(ctx, FCS_EUNSUPPORTED, "factor matrices too large");
+    transpose_all_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(t);
+    rc = check_cuda(ctx, cudaGetLastError(), "transpose_all_kernel");
     if (rc) return rc;
   }
   rc = FCS_EUNSUPPORTED;

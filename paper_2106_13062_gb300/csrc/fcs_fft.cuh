@@ -123,8 +123,14 @@ __device__ __forceinline__ void fft_first_pass(const float *A, int sb, float2 *B
         v[r] = (2 * m < sb) ? A2[m] : make_float2(0.f, 0.f);
       }
       Dft<R>::run(v);
+      if constexpr (R == 16) {
+        float2 *o = B + j * 17;              // pad(16 j + r) = 17 j + r
 #pragma unroll
-      for (int r = 0; r < R; ++r) B[pad(j * R + r)] = v[r];
+        for (int r = 0; r < R; ++r) o[r] = v[r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) B[pad(j * R + r)] = v[r];
+      }
     }
   }
 }
@@ -140,13 +146,17 @@ __device__ __forceinline__ void fft_middle_pass(float2 *B, const float2 *tws) {
   constexpr int NB = M / R;
   constexpr int PER = (NB + NT - 1) / NT;
   const float2 *tp = tws + plan_twoff(L, P);
+  // NB and NS are multiples of 16 here, so pad(x + r*S) = pad(x) + r*(S + S/16)
+  static_assert(NB % 16 == 0 && NS % 16 == 0, "middle pass strides");
+  constexpr int SNB = NB + NB / 16, SNS = NS + NS / 16;
   float2 v[PER][R];
 #pragma unroll
   for (int b = 0; b < PER; ++b) {
     const int j = threadIdx.x + b * NT;
     if (NB % NT == 0 || j < NB) {
+      const float2 *src = B + pad(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = B[pad(j + r * NB)];
+      for (int r = 0; r < R; ++r) v[b][r] = src[r * SNB];
     }
   }
   __syncthreads();
@@ -160,9 +170,9 @@ __device__ __forceinline__ void fft_middle_pass(float2 *B, const float2 *tws) {
       for (int q = 0; q < LR; ++q) wp[q] = tp[q * NS + k];
       twiddle_powers<LR>(v[b], wp);
       Dft<R>::run(v[b]);
-      const int base = (j - k) * R + k;
+      float2 *dst = B + pad((j - k) * R + k);
 #pragma unroll
-      for (int r = 0; r < R; ++r) B[pad(base + r * NS)] = v[b][r];
+      for (int r = 0; r < R; ++r) dst[r * SNS] = v[b][r];
     }
   }
   __syncthreads();
@@ -213,10 +223,20 @@ __device__ __forceinline__ void fft_last_pass_unpack(const float2 *B,
       continue;
     }
     const int j1 = u ? NS - u : NS / 2;
+    if constexpr (NS % 16 == 0) {
+      constexpr int SNS = NS + NS / 16;
+      const float2 *s0 = B + pad(u), *s1 = B + pad(j1);
 #pragma unroll
-    for (int r = 0; r < RL; ++r) {
-      z0[r] = B[pad(u + r * NS)];
-      z1[r] = B[pad(j1 + r * NS)];
+      for (int r = 0; r < RL; ++r) {
+        z0[r] = s0[r * SNS];
+        z1[r] = s1[r * SNS];
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        z0[r] = B[pad(u + r * NS)];
+        z1[r] = B[pad(j1 + r * NS)];
+      }
     }
     if (u != 0) {
       // butterfly u: powers of W_M^u; butterfly NS-u: powers of
@@ -278,5 +298,69 @@ __device__ __forceinline__ int last_pass_index(int e, int b, int r) {
   const int j = b == 0 ? u : (u ? LPs::NS - u : LPs::NS / 2);
   return j + r * LPs::NS;
 }
+
+// Forward real FFT of the compact real buffer A (sb floats, everything past
+// them zero) into slot registers X.  Starts and ends with a barrier; A is
+// cleared (float4 stores; sb a multiple of 4) once the first pass has read it.
+template <int L, int NT>
+__device__ __forceinline__ void rfft_to_slots(float *A, int sb, float2 *B, const float2 *tws,
+                                              const float2 *__restrict__ tw,
+                                              float2 (*X)[2][LastPass<L, NT>::RL]) {
+  __syncthreads();
+  fft_first_pass<L, NT>(A, sb, B);
+  __syncthreads();
+  for (int e = threadIdx.x; e < sb / 4; e += NT)
+    reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  fft_middle_passes<L, NT, 1>(B, tws);
+  fft_last_pass_unpack<L, NT>(B, tw, X);
+  __syncthreads();
+}
+
+// Write slot values X (a half spectrum) into B as the conjugated packed
+// sequence conj(Z) of pack_pair_conj, so that a forward complex FFT of B,
+// conjugated and scaled by 1/M, yields the real inverse transform.  Every
+// pair (q, M-q) lives in one thread.  The caller synchronises afterwards.
+template <int L, int NT>
+__device__ __forceinline__ void slots_to_conj_packed(float2 *B,
+                                                     const float2 (*X)[2][LastPass<L, NT>::RL],
+                                                     const float2 *__restrict__ tw) {
+  using LPs = LastPass<L, NT>;
+  constexpr int M = 1 << L;
+  constexpr int RL = LPs::RL, NS = LPs::NS;
+#pragma unroll
+  for (int e = 0; e < LPs::EPS; ++e) {
+    const int u = threadIdx.x + e * NT;
+    if (LPs::SLOTS % NT != 0 && u >= LPs::SLOTS) continue;
+    if (u != 0) {
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int a = u + r * NS;                  // partner M - a is X[e][1][RL-1-r]
+        if (a < M / 2)
+          pack_pair_conj<L>(B, a, X[e][0][r], X[e][1][RL - 1 - r], tw);
+        else
+          pack_pair_conj<L>(B, M - a, X[e][1][RL - 1 - r], X[e][0][r], tw);
+      }
+    } else {
+      pack_pair_conj<L>(B, 0, X[e][0][0], X[e][0][RL / 2], tw);
+#pragma unroll
+      for (int r = 1; r < RL / 2; ++r)
+        pack_pair_conj<L>(B, r * NS, X[e][0][r], X[e][0][RL - r], tw);
+#pragma unroll
+      for (int r = 0; r < RL / 2; ++r)
+        pack_pair_conj<L>(B, NS / 2 + r * NS, X[e][1][r], X[e][1][RL - 1 - r], tw);
+    }
+  }
+}
+
+// Shared-memory layout for kernels built on rfft_to_slots: B (padded FFT
+// buffer) | twiddle table | A (compact real input of sb floats).
+template <int L>
+struct FftSmem {
+  static constexpr size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
+  static constexpr size_t kB = 0;
+  static constexpr size_t kTw = up16(sizeof(float2) * padded_len(1 << L));
+  static constexpr size_t kA = up16(kTw + sizeof(float2) * plan_twlen(L));
+  static size_t bytes(int sb) { return kA + sizeof(float) * size_t(sb); }
+};
 
 }  // namespace fcs

@@ -303,6 +303,56 @@ __device__ __forceinline__ float median_inplace(float *v) {
   return 0.5f * (v[D / 2 - 1] + v[D / 2]);
 }
 
+// Batcher's odd-even merge sorting network for D values (comparators listed
+// at compile time as (a << 6) | b, applied by template recursion so every
+// index is a constant and the values stay in registers).
+template <int D>
+struct SortNet {
+  static constexpr int count() {
+    int c = 0;
+    for (int p = 1; p < D; p <<= 1)
+      for (int k = p; k >= 1; k >>= 1)
+        for (int j = k % p; j + k < D; j += 2 * k)
+          for (int i = 0; i < k && i < D - j - k; ++i)
+            if ((i + j) / (2 * p) == (i + j + k) / (2 * p)) ++c;
+    return c;
+  }
+  static constexpr int kN = count();
+  struct Arr {
+    int v[kN > 0 ? kN : 1];
+  };
+  static constexpr Arr make() {
+    Arr r{};
+    int c = 0;
+    for (int p = 1; p < D; p <<= 1)
+      for (int k = p; k >= 1; k >>= 1)
+        for (int j = k % p; j + k < D; j += 2 * k)
+          for (int i = 0; i < k && i < D - j - k; ++i)
+            if ((i + j) / (2 * p) == (i + j + k) / (2 * p)) r.v[c++] = ((i + j) << 6) | (i + j + k);
+    return r;
+  }
+  static constexpr Arr net = make();
+};
+
+template <int D, int C>
+__device__ __forceinline__ void sort_net_apply(float *v) {
+  if constexpr (C < SortNet<D>::kN) {
+    constexpr int e = SortNet<D>::net.v[C];
+    const float x = v[e >> 6], y = v[e & 63];
+    v[e >> 6] = fminf(x, y);
+    v[e & 63] = fmaxf(x, y);
+    sort_net_apply<D, C + 1>(v);
+  }
+}
+
+// Median by the sorting network (even D: mean of the two middle values).
+template <int D>
+__device__ __forceinline__ float median_net(float *v) {
+  sort_net_apply<D, 0>(v);
+  if (D & 1) return v[D / 2];
+  return 0.5f * (v[D / 2 - 1] + v[D / 2]);
+}
+
 // ---------------------------------------------------------------- launch helpers
 // Runtime LOG2M -> compile-time dispatch for 3 <= LOG2M <= 13.
 #define FCS_DISPATCH_LOG2M(log2m, BODY)                      \

@@ -4,7 +4,7 @@
 // i.e. the full linear convolution of the two sketches.  One CTA per
 // (batch item, sketch): two real forward FFTs in shared memory, the product
 // kept in registers, one inverse real FFT.
-#include "fcs_internal.cuh"
+#include "fcs_fft.cuh"
 
 namespace fcs {
 namespace {
@@ -12,51 +12,43 @@ namespace {
 template <int LOG2M, int NT>
 __global__ void __launch_bounds__(NT) outer_kernel(const float *__restrict__ fa,
                                                    const float *__restrict__ fb, int64_t La,
-                                                   int64_t Lb, int D, float *__restrict__ out,
+                                                   int64_t Lb, int D, int sb,
+                                                   float *__restrict__ out,
                                                    const float2 *__restrict__ tw) {
+  using LPs = LastPass<LOG2M, NT>;
+  using Lay = FftSmem<LOG2M>;
   constexpr int M = 1 << LOG2M;
-  constexpr int HALF = M / 2;
-  constexpr int EP = (HALF + NT - 1) / NT;
-  extern __shared__ __align__(16) float2 buf[];
-  float *bufr = reinterpret_cast<float *>(buf);
+  constexpr int RL = LPs::RL, EPS = LPs::EPS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2 *B = reinterpret_cast<float2 *>(smem + Lay::kB);
+  float2 *tws = reinterpret_cast<float2 *>(smem + Lay::kTw);
+  float *A = reinterpret_cast<float *>(smem + Lay::kA);
   const int tid = threadIdx.x;
   const int64_t item = int64_t(blockIdx.y) * D + blockIdx.x;   // (b, d)
-  float2 pA[EP], pB[EP];
+  fill_twiddles<LOG2M, NT>(tws, tw);
+  float2 p[EPS][2][RL], X[EPS][2][RL];
   for (int side = 0; side < 2; ++side) {
     const int64_t len = side == 0 ? La : Lb;
     const float *x = (side == 0 ? fa : fb) + item * len;
-    for (int e = tid; e < padded_len(M); e += NT) buf[e] = make_float2(0.f, 0.f);
-    __syncthreads();
-    for (int64_t j = tid; j < len; j += NT) bufr[real_off(int(j))] = __ldg(x + j);
-    __syncthreads();
-    block_fft<LOG2M, NT>(buf, tw);
+    for (int j = tid; j < sb; j += NT) A[j] = j < len ? __ldg(x + j) : 0.f;
+    rfft_to_slots<LOG2M, NT>(A, sb, B, tws, tw, X);
 #pragma unroll
-    for (int e = 0; e < EP; ++e) {
-      const int q = tid + e * NT;
-      if (q < HALF) {
-        float2 A, B;
-        unpack_pair<LOG2M>(buf, q, tw, A, B);
-        if (side == 0) {
-          pA[e] = A;
-          pB[e] = B;
-        } else {
-          pA[e] = slot_mul(pA[e], A, q == 0);
-          pB[e] = cmul(pB[e], B);
+    for (int e = 0; e < EPS; ++e)
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const bool packed = bb == 0 && r == 0 && tid + e * NT == 0;
+          p[e][bb][r] = side == 0 ? X[e][bb][r] : slot_mul(p[e][bb][r], X[e][bb][r], packed);
         }
-      }
-    }
-    __syncthreads();
   }
-#pragma unroll
-  for (int e = 0; e < EP; ++e) {
-    const int q = tid + e * NT;
-    if (q < HALF) pack_pair_conj<LOG2M>(buf, q, pA[e], pB[e], tw);
-  }
+  slots_to_conj_packed<LOG2M, NT>(B, p, tw);
   __syncthreads();
-  block_fft<LOG2M, NT>(buf, tw);
+  block_fft<LOG2M, NT>(B, tw);
   const int64_t Lo = La + Lb - 1;
   float *o = out + item * Lo;
   const float sc = 1.0f / float(M);
+  const float *bufr = reinterpret_cast<const float *>(B);
   for (int64_t j = tid; j < Lo; j += NT) {
     const float v = bufr[real_off(int(j))];
     o[j] = (j & 1) ? -v * sc : v * sc;
@@ -67,15 +59,16 @@ template <int LOG2M>
 int launch_outer(fcs_ctx *ctx, int64_t nbatch, int D, int64_t La, int64_t Lb,
                  const float *fa, const float *fb, float *out) {
   constexpr int NT = fft_threads(LOG2M);
-  const size_t smem = sizeof(float2) * padded_len(1 << LOG2M);
+  const int sb = int(((La > Lb ? La : Lb) + 3) / 4 * 4);
+  const size_t smem = FftSmem<LOG2M>::bytes(sb);
   auto kern = outer_kernel<LOG2M, NT>;
   if (smem > 48 * 1024) {
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(outer)");
   }
-  kern<<<dim3(unsigned(D), unsigned(nbatch)), NT, smem, ctx->stream>>>(fa, fb, La, Lb, D, out,
-                                                                       ctx->twiddle);
+  kern<<<dim3(unsigned(D), unsigned(nbatch)), NT, smem, ctx->stream>>>(fa, fb, La, Lb, D, sb,
+                                                                       out, ctx->twiddle);
   return check_cuda(ctx, cudaGetLastError(), "outer_kernel");
 }
 
