@@ -17,7 +17,9 @@
 // spectrum into a global accumulator with float2 atomics; the last CTA to
 // finish for sketch d (ticket counter) runs the one inverse real FFT and
 // writes FCS_d.  The next column's factor values and hashes are prefetched
-// into registers while the current column is transformed.
+// into registers while the current column is transformed.  For P = 16384
+// the kernel runs on the warp-DIT engine instead (cp13_kernel): two block
+// barriers per transform, the next column scattered between them.
 #include <cstdarg>
 #include <mutex>
 
@@ -35,7 +37,7 @@ struct CpArgs {
   int64_t ut_off[kMaxN];
   const int32_t *h;
   const int8_t *s;
-  float2 *G;             // [D][M+1] spectrum accumulator, zeroed per call
+  float2 *G;             // [D][M+2] spectrum accumulator (bins 0..M), zeroed per call
   unsigned *counter;     // [D] tickets, zero at launch, reset by the last CTA
   float *out;            // [D][Jt]
   int sb;                // scatter buffer length (floats): max J_n rounded up to 4
@@ -60,26 +62,6 @@ __global__ void transpose_all_kernel(TransposeArgs t) {
   float *UT = t.UT + t.ut_off[n];
   const int64_t i0 = blockIdx.x * 32ll, r0 = blockIdx.y * 32ll;
   if (i0 >= I) return;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int64_t i = i0 + k, r = r0 + threadIdx.x;
-    if (i < I && r < R) tile[k][threadIdx.x] = U[i * ld + r];
-  }
-  __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int64_t r = r0 + k, i = i0 + threadIdx.x;
-    if (i < I && r < R) {
-      const float lam = lambda ? __ldg(lambda + r) : 1.f;
-      UT[r * I + i] = tile[threadIdx.x][k] * lam;
-    }
-  }
-}
-
-// UT[n][r][i] = U_n[i*ld + r] (times lambda_r for n = 0).
-__global__ void transpose_factors_kernel(const float *__restrict__ U, int64_t I, int64_t R,
-                                         int64_t ld, const float *__restrict__ lambda,
-                                         float *__restrict__ UT) {
-  __shared__ float tile[32][33];
-  const int64_t i0 = blockIdx.x * 32ll, r0 = blockIdx.y * 32ll;
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
     const int64_t i = i0 + k, r = r0 + threadIdx.x;
     if (i < I && r < R) tile[k][threadIdx.x] = U[i * ld + r];
@@ -211,7 +193,7 @@ __global__ void __launch_bounds__(NT) cp_kernel(CpArgs a, const float2 *__restri
   }
 
   // publish the partial spectrum
-  float2 *Gd = a.G + d * int64_t(M + 1);
+  float2 *Gd = a.G + d * int64_t(M + 2);
 #pragma unroll
   for (int e = 0; e < EPS; ++e) {
     if (LPs::SLOTS % NT != 0 && tid + e * NT >= LPs::SLOTS) continue;
@@ -260,23 +242,256 @@ __global__ void __launch_bounds__(NT) cp_kernel(CpArgs a, const float2 *__restri
   if (tid == 0) a.counter[d] = 0u;
 }
 
+// cp_kernel for P = 16384 on the warp-DIT engine (wdit:: in fcs_fft.cuh):
+// the same work split, prefetch, rank accumulation and last-CTA inverse, but
+// two block barriers per transform.  The next column is scattered into the
+// row-wise buffer between them, overlapping step 2 of the current one.
+// RMAX = number of 32-entry blocks per scatter-buffer row (ra <= 32 RMAX).
+struct Cp13Smem {
+  static constexpr size_t kB = 0;                                   // 16 x kRS float2
+  static constexpr size_t kAcc = kB + sizeof(float2) * 16 * wdit::kRS;
+  static constexpr size_t kTw = kAcc + sizeof(float2) * 16 * wdit::kNT;
+  static constexpr size_t kStash = kTw + sizeof(float2) * wdit::kTwLen;
+  static constexpr size_t kA = kStash + sizeof(float2) * 16;
+  static size_t bytes(int ra) { return kA + sizeof(float2) * 16 * size_t(ra); }
+};
+
+template <int CPT, int RMAX>
+__global__ void __launch_bounds__(wdit::kNT) cp13_kernel(CpArgs a, const float2 *__restrict__ tw) {
+  constexpr int NT = wdit::kNT, M = wdit::kM, HALF = M / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *B = reinterpret_cast<float2 *>(smem_raw + Cp13Smem::kB);
+  float4 *acc4 = reinterpret_cast<float4 *>(smem_raw + Cp13Smem::kAcc);   // [8][NT] pairs
+  float2 *tws = reinterpret_cast<float2 *>(smem_raw + Cp13Smem::kTw);
+  float2 *stash = reinterpret_cast<float2 *>(smem_raw + Cp13Smem::kStash);
+  float2 *A2 = reinterpret_cast<float2 *>(smem_raw + Cp13Smem::kA);
+  float *A = reinterpret_cast<float *>(A2);
+  __shared__ int is_last;
+  const int tid = threadIdx.x;
+  const int d = blockIdx.y;
+  const int N = a.m.N;
+  const int64_t r0 = blockIdx.x * a.ranks_per_cta;
+  const int64_t r1 = min(a.R, r0 + a.ranks_per_cta);
+  const int sb = a.sb;
+  const int ra = (sb + 31) >> 5;
+
+  float pv[CPT];
+  int ph[CPT];
+  auto fetch = [&](int64_t r, int n) {
+    const int64_t In = a.m.I[n];
+    const float *col = a.UT + a.ut_off[n] + r * In;
+    const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
+    const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int64_t i = tid + int64_t(c) * NT;
+      ph[c] = -1;
+      pv[c] = 0.f;
+      if (i < In) {
+        const float v = __ldg(col + i);
+        pv[c] = __ldg(sn + i) < 0 ? -v : v;
+        ph[c] = __ldg(hn + i);
+      }
+    }
+  };
+  // scatter the fetched column (and, for I_n > CPT NT, the rest of it)
+  auto scatter = [&](int64_t r, int n) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (unsigned(ph[c]) < unsigned(sb)) atomicAdd(A + wdit::a_index(ph[c], ra), pv[c]);
+    const int64_t In = a.m.I[n];
+    if (In > int64_t(CPT) * NT) {
+      const float *col = a.UT + a.ut_off[n] + r * In;
+      const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
+      const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
+      for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
+        const int hb = __ldg(hn + i);
+        const float v = __ldg(col + i);
+        if (unsigned(hb) < unsigned(sb))
+          atomicAdd(A + wdit::a_index(hb, ra), __ldg(sn + i) < 0 ? -v : v);
+      }
+    }
+  };
+  // the first column's loads and the twiddle loads overlap
+  fetch(r0, 0);
+  wdit::fill_twiddles(tws, tw);
+  for (int e = tid; e < 16 * ra; e += NT) A2[e] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc4[q * NT + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  scatter(r0, 0);
+  __syncthreads();
+
+  float2 p[16];
+  for (int64_t r = r0; r < r1; ++r) {
+    for (int n = 0; n < N; ++n) {
+      // the scatter buffer holds column (r, n); fetch the next one
+      int64_t rn = r;
+      int nn = n + 1;
+      if (nn == N) {
+        nn = 0;
+        ++rn;
+      }
+      const bool more = rn < r1;
+      if (more) fetch(rn, nn);
+      wdit::step1<RMAX>(A2, ra, B, tws);
+      __syncthreads();
+      // warps 0-7 scatter the next column before step 2, warps 8-15 after it,
+      // so each scheduler overlaps the atomics' latency with step-2 work
+      const bool early = tid < NT / 2;
+      if (more && early) scatter(rn, nn);
+      float2 v[16];
+      wdit::step2(B, tws, stash, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (n == 0)
+          p[j] = v[j];
+        else
+          p[j] = slot_mul(p[j], v[j], tid == 0 && j == 0);
+      }
+      if (n == N - 1) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float4 &acc = acc4[q * NT + tid];
+          float4 x = acc;
+          x.x += p[2 * q].x;
+          x.y += p[2 * q].y;
+          x.z += p[2 * q + 1].x;
+          x.w += p[2 * q + 1].y;
+          acc = x;
+        }
+      }
+      if (more && !early) scatter(rn, nn);
+      __syncthreads();
+    }
+  }
+
+  // publish the partial spectrum as 16-byte atomics over bin pairs (k, k+1);
+  // value j of thread t is 2^N X[spectrum_index(q2(t), j)]
+  float2 *Gd = a.G + d * int64_t(M + 2);
+  const float2 *accv = reinterpret_cast<const float2 *>(acc4);
+  auto acc_at = [&](int k) -> float2 {       // accumulated value of bin k (k < M)
+    const int jj = k >> 9, c = k & 511;
+    const int q2 = jj < 8 ? c : wdit::q2_partner(c);
+    const int u = q2 <= 256 ? (q2 == 256 ? 0 : q2) : 512 - q2;
+    const int e = q2 >= 256 ? 1 : 0;
+    const int t = ((u >> 4) << 5) | (e << 4) | (u & 15);
+    return accv[((jj >> 1) * NT + t) * 2 + (jj & 1)];
+  };
+  for (int f = tid; f < M / 2; f += NT) {
+    const float2 x0 = acc_at(2 * f), x1 = acc_at(2 * f + 1);
+    if (f == 0) {
+      atomicAdd(&Gd[M].x, x0.y);            // bin M (packed with bin 0)
+      atomicAdd(reinterpret_cast<float4 *>(Gd), make_float4(x0.x, 0.f, x1.x, x1.y));
+    } else {
+      atomicAdd(reinterpret_cast<float4 *>(Gd) + f, make_float4(x0.x, x0.y, x1.x, x1.y));
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = (atomicAdd(&a.counter[d], 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+
+  // last CTA for sketch d: one inverse real FFT of the summed spectrum on the
+  // same engine.  The conj-packed sequence goes row-wise (ra = 512) into the
+  // accumulator region; a forward complex FFT, conj and scaling give FCS_d.
+  float2 *Z2 = reinterpret_cast<float2 *>(acc4);
+  {
+    // all (coalesced) loads first: one L2 round trip
+    constexpr int PER = HALF / NT;
+    float2 Av[PER], Bv[PER], Wv[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int q = k * NT + tid;
+      if (q == 0) {
+        Av[k] = make_float2(__ldcg(&Gd[0].x), __ldcg(&Gd[M].x));
+        Bv[k] = __ldcg(&Gd[HALF]);
+        Wv[k] = make_float2(1.f, 0.f);
+      } else {
+        Av[k] = __ldcg(&Gd[q]);
+        Bv[k] = __ldcg(&Gd[M - q]);
+        Wv[k] = __ldg(&tw[q << (kLogTwN - wdit::kL - 1)]);   // W_P^q
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int q = k * NT + tid;
+      float2 cq, cm;
+      pack_pair_conj_values_w(q, Av[k], Bv[k], Wv[k], cq, cm);
+      Z2[wdit::row_pos_swz(q)] = cq;
+      Z2[wdit::row_pos_swz(q ? M - q : HALF)] = cm;
+    }
+  }
+  __syncthreads();
+  wdit::step1<16, true>(Z2, 512, B, tws);
+  __syncthreads();
+  float2 v[16];
+  wdit::step2_complex(B, tws, v);                   // v[q1] = Z[q2 + 512 q1]
+  // 1/M of the inverse and 2^-N for the doubled unpack of every mode
+  const float sc = 1.0f / float(int64_t(M) << N);
+  float *od = a.out + d * a.m.Jt;
+  const int64_t Jt = a.m.Jt;
+  const int q2 = wdit::q2_of(tid);
+#pragma unroll
+  for (int q1 = 0; q1 < 16; ++q1) {
+    const int64_t m = q2 + 512 * q1;
+    if (2 * m < Jt) od[2 * m] = v[q1].x * sc;
+    if (2 * m + 1 < Jt) od[2 * m + 1] = -v[q1].y * sc;
+  }
+  if (tid == 0) a.counter[d] = 0u;
+}
+
+// Kernel for the given prefetch depth and scatter-buffer height.
+template <int CPT>
+const void *cp13_pick_rmax(int ra) {
+  if (ra <= 128) return reinterpret_cast<const void *>(cp13_kernel<CPT, 4>);
+  if (ra <= 256) return reinterpret_cast<const void *>(cp13_kernel<CPT, 8>);
+  return reinterpret_cast<const void *>(cp13_kernel<CPT, 16>);
+}
+const void *cp13_pick(int64_t Imax, int sb) {
+  const int ra = (sb + 31) >> 5;
+  const int cpt = int((Imax + wdit::kNT - 1) / wdit::kNT);
+  if (cpt <= 1) return cp13_pick_rmax<1>(ra);
+  if (cpt <= 2) return cp13_pick_rmax<2>(ra);
+  return cp13_pick_rmax<4>(ra);
+}
+
+int launch_cp13(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
+  const size_t smem = Cp13Smem::bytes((a.sb + 31) >> 5);
+  const void *kern = cp13_pick(Imax, a.sb);
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp13)");
+  const float2 *twp = ctx->twiddle;
+  void *args[] = {&a, &twp};
+  e = cudaLaunchKernel(kern, dim3(unsigned(groups), unsigned(a.D)), dim3(wdit::kNT), args, smem,
+                       ctx->stream);
+  return check_cuda(ctx, e, "cp13_kernel");
+}
+
 template <int LOG2M>
 int launch_cp(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
-  constexpr int NT = fft_threads(LOG2M);
-  const size_t smem = CpSmem<LOG2M, NT>::bytes(a.sb);
-  const int cpt = int((Imax + NT - 1) / NT);
-  auto go = [&](auto kern) -> int {
-    if (smem > 48 * 1024) {
-      cudaError_t e =
-          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp)");
-    }
-    kern<<<dim3(unsigned(groups), unsigned(a.D)), NT, smem, ctx->stream>>>(a, ctx->twiddle);
-    return check_cuda(ctx, cudaGetLastError(), "cp_kernel");
-  };
-  if (cpt <= 1) return go(cp_kernel<LOG2M, NT, 1>);
-  if (cpt <= 2) return go(cp_kernel<LOG2M, NT, 2>);
-  return go(cp_kernel<LOG2M, NT, 4>);       // larger modes add a direct tail loop
+  if constexpr (LOG2M == wdit::kL) {
+    return launch_cp13(ctx, a, groups, Imax);
+  } else {
+    constexpr int NT = fft_threads(LOG2M);
+    const size_t smem = CpSmem<LOG2M, NT>::bytes(a.sb);
+    const int cpt = int((Imax + NT - 1) / NT);
+    auto go = [&](auto kern) -> int {
+      if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp)");
+      }
+      kern<<<dim3(unsigned(groups), unsigned(a.D)), NT, smem, ctx->stream>>>(a, ctx->twiddle);
+      return check_cuda(ctx, cudaGetLastError(), "cp_kernel");
+    };
+    if (cpt <= 1) return go(cp_kernel<LOG2M, NT, 1>);
+    if (cpt <= 2) return go(cp_kernel<LOG2M, NT, 2>);
+    return go(cp_kernel<LOG2M, NT, 4>);       // larger modes add a direct tail loop
+  }
 }
 
 }  // namespace
@@ -329,7 +544,7 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
     if (host_J[n] > Jmax) Jmax = host_J[n];
   }
   a.sb = int((Jmax + 3) / 4 * 4);
-  const size_t gbytes = (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
+  const size_t gbytes = (sizeof(float2) * size_t(D) * size_t(M + 2) + 255) & ~size_t(255);
   const size_t cbytes = 256;
   void *ws = nullptr;
   rc = ensure_workspace(ctx, gbytes + cbytes + sizeof(float) * size_t(utlen), &ws);
@@ -450,7 +665,8 @@ template <int LOG2M>
 int noalloc_launch_cp(CpArgs &a, int64_t groups, int64_t Imax, const float2 *tw,
                       cudaStream_t st, char *err, size_t n) {
   constexpr int NT = fft_threads(LOG2M);
-  const size_t smem = CpSmem<LOG2M, NT>::bytes(a.sb);
+  const size_t smem = LOG2M == wdit::kL ? Cp13Smem::bytes((a.sb + 31) >> 5)
+                                        : CpSmem<LOG2M, NT>::bytes(a.sb);
   const int cpt = int((Imax + NT - 1) / NT);
   auto go = [&](auto kern) -> int {
     if (smem > 48 * 1024) {
@@ -465,9 +681,22 @@ int noalloc_launch_cp(CpArgs &a, int64_t groups, int64_t Imax, const float2 *tw,
       return noalloc_fail(err, n, FCS_ECUDA, "cp_kernel: %s", cudaGetErrorString(e));
     return FCS_OK;
   };
-  if (cpt <= 1) return go(cp_kernel<LOG2M, NT, 1>);
-  if (cpt <= 2) return go(cp_kernel<LOG2M, NT, 2>);
-  return go(cp_kernel<LOG2M, NT, 4>);
+  if constexpr (LOG2M == wdit::kL) {
+    const void *kern = cp13_pick(Imax, a.sb);
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess)
+      return noalloc_fail(err, n, FCS_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    void *args[] = {&a, &tw};
+    e = cudaLaunchKernel(kern, dim3(unsigned(groups), unsigned(a.D)), dim3(NT), args, smem, st);
+    if (e != cudaSuccess)
+      return noalloc_fail(err, n, FCS_ECUDA, "cp13_kernel: %s", cudaGetErrorString(e));
+    return FCS_OK;
+  } else {
+    if (cpt <= 1) return go(cp_kernel<LOG2M, NT, 1>);
+    if (cpt <= 2) return go(cp_kernel<LOG2M, NT, 2>);
+    return go(cp_kernel<LOG2M, NT, 4>);
+  }
 }
 
 }  // namespace
@@ -508,7 +737,7 @@ extern "C" int fcs_sketch_cp_noalloc(void *stream, int N, const int64_t *host_I,
     if (host_I[n] > Imax) Imax = host_I[n];
     if (host_J[n] > Jmax) Jmax = host_J[n];
   }
-  const size_t gbytes = (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
+  const size_t gbytes = (sizeof(float2) * size_t(D) * size_t(M + 2) + 255) & ~size_t(255);
   const size_t cbytes = 256;
   const size_t need = gbytes + cbytes + sizeof(float) * size_t(utlen);
   if (need > kNoAllocScratchBytes)
@@ -547,11 +776,20 @@ extern "C" int fcs_sketch_cp_noalloc(void *stream, int N, const int64_t *host_I,
   e = cudaMemsetAsync(sd->scratch, 0, gbytes + cbytes, st);
   if (e != cudaSuccess)
     return noalloc_fail(err, err_len, FCS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
-  for (int n = 0; n < N; ++n) {
-    dim3 grid(unsigned((host_I[n] + 31) / 32), unsigned((R + 31) / 32));
+  {
+    TransposeArgs t{};
+    for (int n = 0; n < N; ++n) {
+      t.U[n] = host_U[n];
+      t.I[n] = host_I[n];
+      t.ld[n] = host_ldU[n];
+      t.ut_off[n] = a.ut_off[n];
+    }
+    t.R = R;
+    t.lambda = lambda;
+    t.UT = UT;
+    dim3 grid(unsigned((Imax + 31) / 32), unsigned((R + 31) / 32), unsigned(N));
     if (grid.y > 65535) return noalloc_fail(err, err_len, FCS_EUNSUPPORTED, "rank too large");
-    transpose_factors_kernel<<<grid, dim3(32, 8), 0, st>>>(
-        host_U[n], host_I[n], R, host_ldU[n], n == 0 ? lambda : nullptr, UT + a.ut_off[n]);
+    transpose_all_kernel<<<grid, dim3(32, 8), 0, st>>>(t);
     e = cudaGetLastError();
     if (e != cudaSuccess)
       return noalloc_fail(err, err_len, FCS_ECUDA, "transpose: %s", cudaGetErrorString(e));

@@ -363,4 +363,247 @@ struct FftSmem {
   static size_t bytes(int sb) { return kA + sizeof(float) * size_t(sb); }
 };
 
+// ---------------------------------------------------------------- warp-DIT engine
+// A second forward real FFT for the largest size, P = 16384 (M = 8192), with
+// one block barrier per transform instead of one per pass.  Decimation in
+// time splits z into the 16 sub-sequences z_w[m2] = z[16 m2 + w]:
+//   Z[k + 512 q1] = sum_w W16^(w q1) W_M^(w k) Y_w[k],   Y_w = FFT_512(z_w).
+// Step 1 (warp-local): warp w computes Y_w, 16 values per lane, as
+//   Y_w[ka + 16 kb] = sum_l W32^(l kb) W512^(l ka) sum_r W16^(r ka) z_w[l + 32 r]:
+//   a radix-16 DFT over r in registers (input-pruned: rows r >= RMAX of the
+//   scatter buffer are empty), the twiddle W512^(l ka), a transpose through
+//   a warp-private stretch of B (__syncwarp only), then the 16 32-point DFTs
+//   over l split between the two half-warps (half e takes the outputs
+//   kb = 2 kk + e after one radix-2 step); Y_w goes to row w of B.
+// Step 2 (after one block barrier): thread t owns column q2(t) of B, applies
+//   W_M^(w q2) and the radix-16 DFT over w, which leaves Z[q2 + 512 q1] in its
+//   registers.  Lane l and lane l ^ 16 hold q2 = u and 512 - u, so every
+//   real-FFT unpack pair (q, M - q) spans the two lanes: each lane finishes
+//   the pairs of its q1 < 8, receiving 8 values from its neighbour (q2 = 0
+//   and q2 = 256 pair with themselves).
+// The input is the real scatter buffer seen as z[m] = x[2m] + i x[2m+1],
+// stored row-wise: z[m] at float2 index (m mod 16) ra + m / 16, ra >= sb/32.
+namespace wdit {
+
+constexpr int kL = 13;
+constexpr int kM = 1 << kL;
+constexpr int kNT = 512;
+constexpr int kRS = 576;     // row stride of B (float2); B also serves the padded block FFT
+constexpr int kTR = 18;      // row stride of the step-1 transpose (float2, even: 16-byte pairs)
+constexpr int kTw2 = 16 * 32;               // start of the step-2 part of the table
+constexpr int kTwLen = kTw2 + 5 * kNT;      // per-CTA twiddle table (float2)
+static_assert(16 * kRS >= padded_len(kM), "B doubles as the padded block-FFT buffer");
+static_assert(31 * kTR + 16 <= kRS, "transpose fits in one row of B");
+
+// Float index of real sample h in the row-wise scatter buffer.
+__device__ __forceinline__ int a_index(int h, int ra) {
+  const int m = h >> 1;
+  return 2 * ((m & 15) * ra + (m >> 4)) + (h & 1);
+}
+
+// Column of B owned by thread t in step 2: u = 16 (t / 32) + t mod 16 and
+// half-warp e = (t / 16) mod 2 give q2 = u (e = 0) or 512 - u (e = 1; 256
+// for u = 0).
+__device__ __forceinline__ int q2_of(int t) {
+  const int u = ((t >> 5) << 4) | (t & 15);
+  return ((t >> 4) & 1) == 0 ? u : (u == 0 ? 256 : 512 - u);
+}
+// Column of the unpack partner (itself for q2 = 0 and 256).
+__device__ __forceinline__ int q2_partner(int q2) {
+  return (q2 & 255) == 0 ? q2 : 512 - q2;
+}
+// Spectrum index held in v[j] after step 2 by a thread owning column q2.
+__device__ __forceinline__ int spectrum_index(int q2, int j) {
+  return (j < 8 ? q2 : q2_partner(q2)) + 512 * j;
+}
+
+// Per-CTA twiddle table: W512^(l ka) at ka*32 + l (ka < 16, l < 32); then
+// for thread t, W_M^(q2(t) 2^b) at kTw2 + b*512 + t (b < 4) and W_P^q2(t) at
+// kTw2 + 4*512 + t.  Filled from the global table tw[k] = exp(-2 pi i k / 2^15).
+// All loads are issued before the first store (one memory round trip).
+// Called by all kNT threads.
+__device__ __forceinline__ void fill_twiddles(float2 *tws, const float2 *__restrict__ tw) {
+  constexpr int PER = kTwLen / kNT;
+  static_assert(kTwLen % kNT == 0, "twiddle table fill");
+  float2 v[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int e = threadIdx.x + k * kNT;
+    if (e < kTw2) {
+      const int ka = e >> 5, l = e & 31;
+      v[k] = __ldg(&tw[(l * ka) << (kLogTwN - 9)]);
+    } else {
+      const int b = (e - kTw2) >> 9, q2 = q2_of((e - kTw2) & (kNT - 1));
+      v[k] = b < 4 ? __ldg(&tw[(q2 << b) << (kLogTwN - kL)])
+                   : __ldg(&tw[q2 << (kLogTwN - kL - 1)]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) tws[threadIdx.x + k * kNT] = v[k];
+}
+
+// Position of z[m] in a full-height row-wise buffer (ra = 512) whose rows
+// are XOR-swizzled: row w holds z[16 m2 + w] at column m2 ^ w, so that 16
+// consecutive m (16 rows, one column) land in distinct banks.  Read back by
+// step1<16, true>.
+__device__ __forceinline__ int row_pos_swz(int m) {
+  const int w = m & 15;
+  return w * 512 + ((m >> 4) ^ w);
+}
+
+// DFT of size R whose inputs v[NZ..R-1] are zero (input-pruned radix-2
+// decimation in time; entries at or past NZ are not read).
+template <int R, int NZ>
+struct DftNZ {
+  static __device__ __forceinline__ void run(float2 *v) {
+    if constexpr (NZ >= R) {
+      Dft<R>::run(v);
+    } else if constexpr (NZ <= 0) {
+#pragma unroll
+      for (int k = 0; k < R; ++k) v[k] = make_float2(0.f, 0.f);
+    } else if constexpr (NZ == 1) {
+#pragma unroll
+      for (int k = 1; k < R; ++k) v[k] = v[0];
+    } else {
+      float2 e[R / 2], o[R / 2];
+#pragma unroll
+      for (int k = 0; k < R / 2; ++k) {
+        e[k] = v[2 * k];
+        o[k] = v[2 * k + 1];
+      }
+      DftNZ<R / 2, (NZ + 1) / 2>::run(e);
+      DftNZ<R / 2, NZ / 2>::run(o);
+#pragma unroll
+      for (int k = 0; k < R / 2; ++k) {
+        float2 t;
+        if (k == 0) {
+          t = o[k];
+        } else if (4 * k == R) {
+          t = make_float2(o[k].y, -o[k].x);
+        } else {
+          const int j = k * (64 / R);
+          t = cmul(o[k], make_float2(cos64(j), -sin64(j)));
+        }
+        v[k] = cadd(e[k], t);
+        v[k + R / 2] = csub(e[k], t);
+      }
+    }
+  }
+};
+
+// Step 1.  Reads (and clears) row w of the scatter buffer A2 (ra <= 32 RMAX
+// float2), writes Y_w[k] to B[w kRS + k].  No block barrier inside.
+// With SWZ the rows are XOR-swizzled as written by row_pos_swz (ra = 512).
+template <int RMAX, bool SWZ = false>
+__device__ __forceinline__ void step1(float2 *A2, int ra, float2 *B, const float2 *tws) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int lc = SWZ ? (l ^ w) : l;                 // column of m2 = l + 32 r, minus 32 r
+  float2 v[16];
+  float2 *row = A2 + w * ra;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int m2 = l + 32 * r;
+    v[r] = (r < RMAX && m2 < ra) ? row[lc + 32 * r] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    const int m2 = l + 32 * r;
+    if (m2 < ra) row[lc + 32 * r] = make_float2(0.f, 0.f);
+  }
+  DftNZ<16, RMAX>::run(v);
+#pragma unroll
+  for (int ka = 1; ka < 16; ++ka) v[ka] = cmul(v[ka], tws[ka * 32 + l]);   // W512^(l ka)
+  float2 *T = B + w * kRS;
+#pragma unroll
+  for (int ka = 0; ka < 16; ka += 2)
+    *reinterpret_cast<float4 *>(T + l * kTR + ka) =
+        make_float4(v[ka].x, v[ka].y, v[ka + 1].x, v[ka + 1].y);
+  __syncwarp();
+  const int j = l & 15;
+  const bool odd = l >= 16;
+  const float sg = odd ? -1.f : 1.f;
+#pragma unroll
+  for (int lp = 0; lp < 16; ++lp) {
+    const float2 a = T[lp * kTR + j], b = T[(lp + 16) * kTR + j];
+    float2 g = make_float2(fmaf(sg, b.x, a.x), fmaf(sg, b.y, a.y));      // a + (-1)^e b
+    if (lp > 0) {
+      const float2 w = unit64(2 * lp);                                  // W32^(lp e)
+      g = cmul(g, make_float2(odd ? w.x : 1.f, odd ? w.y : 0.f));
+    }
+    v[lp] = g;
+  }
+  Dft<16>::run(v);                                  // v[kk] = Y_w[j + 16 e + 32 kk]
+  __syncwarp();
+  const int k0 = j + (odd ? 16 : 0);
+#pragma unroll
+  for (int kk = 0; kk < 16; ++kk) T[k0 + 32 * kk] = v[kk];
+}
+
+// Step 2 up to the complex spectrum: v[q1] = Z[q2 + 512 q1], q2 = q2_of(threadIdx.x).
+__device__ __forceinline__ void step2_complex(const float2 *B, const float2 *tws,
+                                              float2 (&v)[16]) {
+  const int t = threadIdx.x;
+  const int q2 = q2_of(t);
+#pragma unroll
+  for (int w = 0; w < 16; ++w) v[w] = B[w * kRS + q2];
+  {
+    float2 wp[4];                                   // W_M^(q2 2^b)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) wp[b] = tws[kTw2 + b * kNT + t];
+    twiddle_powers<4>(v, wp);
+  }
+  Dft<16>::run(v);
+}
+
+// Twice the real-FFT unpack of one pair: with w = W_P^q,
+// 2 X[q] = 2E + w 2O and 2 X[M - q] = conj(2E - w 2O).
+__device__ __forceinline__ void unpack2_twice(float2 za, float2 zb, float2 w, float2 &xa,
+                                              float2 &xb) {
+  const float2 e = make_float2(za.x + zb.x, za.y - zb.y);
+  const float2 o = make_float2(za.y + zb.y, zb.x - za.x);
+  const float2 t = cmul(w, o);
+  xa = cadd(e, t);
+  xb = cconj(csub(e, t));
+}
+
+// Step 2.  Leaves in v[j] TWICE the half-spectrum value X[spectrum_index(q2, j)]
+// of the real input, q2 = q2_of(threadIdx.x) (the factor 2 saves the halvings
+// of the unpack; callers divide it out at the end); for thread 0, v[0] packs
+// the two real bins (2 X[0], 2 X[M]).  `stash` is 16 float2 of shared scratch
+// used by thread 0.  Every lane of every warp must call it (it shuffles).
+__device__ __forceinline__ void step2(const float2 *B, const float2 *tws, float2 *stash,
+                                      float2 (&v)[16]) {
+  const int t = threadIdx.x;
+  step2_complex(B, tws, v);                         // v[q1] = Z[q2 + 512 q1]
+  if (t == 0) {
+#pragma unroll
+    for (int q1 = 0; q1 < 16; ++q1) stash[q1] = v[q1];
+  }
+  const int lane = t & 31;
+  const bool self = t < 32 && (lane & 15) == 0;     // q2 = 0 or 256
+  const int src = self ? lane : (lane ^ 16);
+  const float2 wP = tws[kTw2 + 4 * kNT + t];        // W_P^q2
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    // Z[M - (q2 + 512 i)] = Z[q2p + 512 (15 - i)] is the partner's v[15 - i]
+    float2 zm;
+    zm.x = __shfl_sync(0xffffffffu, v[15 - i].x, src);
+    zm.y = __shfl_sync(0xffffffffu, v[15 - i].y, src);
+    // W_P^(q2 + 512 i) = W_P^q2 exp(-2 pi i i / 32)
+    const float2 wq = i == 0 ? wP : cmul(wP, unit64(2 * i));
+    unpack2_twice(v[i], zm, wq, v[i], v[15 - i]);  // 2 X[q], 2 X[M - q]
+  }
+  if (t == 0) {
+    // q2 = 0: Z[512 q1] pairs with Z[512 (16 - q1)]; q1 = 0 and 8 pair with themselves
+    const float2 z0 = stash[0], z8 = stash[8];
+    v[0] = make_float2(2.f * (z0.x + z0.y), 2.f * (z0.x - z0.y));
+    v[8] = make_float2(2.f * z8.x, -2.f * z8.y);
+#pragma unroll
+    for (int q1 = 1; q1 < 8; ++q1)
+      unpack2_twice(stash[q1], stash[16 - q1], unit64(2 * q1), v[q1], v[16 - q1]);
+  }
+}
+
+}  // namespace wdit
+
 }  // namespace fcs

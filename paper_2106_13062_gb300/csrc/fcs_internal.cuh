@@ -254,26 +254,41 @@ __device__ __forceinline__ void unpack_pair(const float2 *buf, int q,
 // by conj and 1/M scaling yields z (hence x).  With
 //   E = (X[q] + conj X[M-q]) / 2,  O = (X[q] - conj X[M-q]) conj(W^q) / 2,
 //   Z[q] = E + i O,  Z[M-q] = conj(E) + i conj(O).
+// The two values pack_pair_conj writes for pair q: cq goes to position q and
+// cm to position M - q (for q = 0: positions 0 and M/2).
+// w = W_P^q (unused for q = 0).
+__device__ __forceinline__ void pack_pair_conj_values_w(int q, float2 A, float2 B, float2 w,
+                                                        float2 &cq, float2 &cm) {
+  if (q == 0) {
+    const float e = 0.5f * (A.x + A.y), o = 0.5f * (A.x - A.y);
+    cq = make_float2(e, -o);                   // conj(e + i o)
+    cm = B;                                    // Z[M/2] = conj(X[M/2]); conj again
+  } else {
+    const float2 e = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+    const float2 dd = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y + B.y));
+    const float2 o = cmulconj(dd, w);
+    // Z[q] = e + i o = (e.x - o.y, e.y + o.x);  Z[M-q] = conj(e) + i conj(o)
+    cq = make_float2(e.x - o.y, -(e.y + o.x));
+    cm = make_float2(e.x + o.y, -(o.x - e.y));
+  }
+}
+
+template <int LOG2M>
+__device__ __forceinline__ void pack_pair_conj_values(int q, float2 A, float2 B,
+                                                      const float2 *__restrict__ tw,
+                                                      float2 &cq, float2 &cm) {
+  const float2 w = q ? __ldg(&tw[q << (kLogTwN - LOG2M - 1)]) : make_float2(1.f, 0.f);
+  pack_pair_conj_values_w(q, A, B, w, cq, cm);
+}
+
 template <int LOG2M>
 __device__ __forceinline__ void pack_pair_conj(float2 *buf, int q, float2 A, float2 B,
                                                const float2 *__restrict__ tw) {
   constexpr int M = 1 << LOG2M;
-  if (q == 0) {
-    const float e = 0.5f * (A.x + A.y), o = 0.5f * (A.x - A.y);
-    buf[pad(0)] = make_float2(e, -o);          // conj(e + i o)
-    buf[pad(M / 2)] = B;                       // Z[M/2] = conj(X[M/2]); conj again
-  } else {
-    const float2 e = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
-    const float2 dd = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y + B.y));
-    const float2 w = __ldg(&tw[q << (kLogTwN - LOG2M - 1)]);
-    const float2 o = cmulconj(dd, w);
-    // Z[q] = e + i o = (e.x - o.y, e.y + o.x)
-    const float2 zq = make_float2(e.x - o.y, e.y + o.x);
-    // Z[M-q] = conj(e) + i conj(o) = (e.x + o.y, -e.y + o.x)
-    const float2 zm = make_float2(e.x + o.y, o.x - e.y);
-    buf[pad(q)] = cconj(zq);
-    buf[pad(M - q)] = cconj(zm);
-  }
+  float2 cq, cm;
+  pack_pair_conj_values<LOG2M>(q, A, B, tw, cq, cm);
+  buf[pad(q)] = cq;
+  buf[pad(q ? M - q : M / 2)] = cm;
 }
 
 // Product of two slot values; slot A of pair 0 packs two reals.

@@ -162,6 +162,14 @@ def test_cp_tiny_and_dense_agree(fcs, ctx, orc):
     ([5, 6, 7], [2, 3, 4], 2, 1, {}),                    # Jt = 7, P = 16
     ([200, 200, 200], [5000, 5000, 5000], 5, 2, {}),     # P = 16384
     ([90, 70, 80], [1500, 1200, 1000], 33, 4, {}),       # P = 4096, many ranks
+    # P = 16384 (warp-DIT engine): order 1 with a tail beyond the prefetch,
+    # uneven orders 2 and 4, few ranks with D = 16, and the full-width
+    # scatter buffer (J = P)
+    ([3000], [12000], 3, 2, {}),
+    ([700, 900], [9000, 7000], 6, 3, {"lam_none": True}),
+    ([40, 700, 30, 1200], [4000, 3000, 2000, 5000], 4, 2, {"ld_pad": 3}),
+    ([50, 60, 70], [8192, 4096, 2048], 2, 16, {}),
+    ([100], [16384], 2, 1, {}),
 ])
 def test_cp_shapes(fcs, ctx, orc, I, J, R, D, kw):
     _cp_case(fcs, ctx, orc, I, J, R, D, 21, **kw)
