@@ -473,20 +473,7 @@ struct DftNZ {
       }
       DftNZ<R / 2, (NZ + 1) / 2>::run(e);
       DftNZ<R / 2, NZ / 2>::run(o);
-#pragma unroll
-      for (int k = 0; k < R / 2; ++k) {
-        float2 t;
-        if (k == 0) {
-          t = o[k];
-        } else if (4 * k == R) {
-          t = make_float2(o[k].y, -o[k].x);
-        } else {
-          const int j = k * (64 / R);
-          t = cmul(o[k], make_float2(cos64(j), -sin64(j)));
-        }
-        v[k] = cadd(e[k], t);
-        v[k + R / 2] = csub(e[k], t);
-      }
+      DftCombine<R>::run(v, e, o);
     }
   }
 };

@@ -112,6 +112,70 @@ __host__ __device__ constexpr float sin64(int j) {
   return j <= 16 ? cos64_q(16 - j) : cos64_q(j - 16);
 }
 
+// tan(2 pi j / 64) for j = 0..8.
+__host__ __device__ constexpr float tan64_q(int j) {
+  constexpr float t[9] = {0.0f,
+                          0.09849140335716425f,
+                          0.198912367379658f,
+                          0.3033466836073424f,
+                          0.41421356237309503f,
+                          0.5345111359507916f,
+                          0.6681786379192989f,
+                          0.8206787908286602f,
+                          1.0f};
+  return t[j];
+}
+
+// Radix-2 butterfly a' = a + W b, b' = a - W b with W = exp(-2 pi i J / 64),
+// 0 < J < 32, J != 16, in six FMAs: with c = cos, s = sin of 2 pi J / 64,
+//   W b = c (b.x + (s/c) b.y, b.y - (s/c) b.x)   when |c| >= |s|,
+//   W b = s ((c/s) b.x + b.y, (c/s) b.y - b.x)   otherwise,
+// so the ratio is a tangent of magnitude <= 1.
+template <int J>
+__device__ __forceinline__ void bfly_tw(float2 &a, float2 &b) {
+  static_assert(J > 0 && J < 32 && J != 16, "twiddle index");
+  float f, ux, uy;
+  if constexpr (J <= 8 || J >= 24) {
+    constexpr float t = J <= 8 ? tan64_q(J) : -tan64_q(32 - J);     // s / c
+    f = cos64(J);
+    ux = fmaf(t, b.y, b.x);
+    uy = fmaf(-t, b.x, b.y);
+  } else {
+    constexpr float k = J <= 16 ? tan64_q(16 - J) : -tan64_q(J - 16);   // c / s
+    f = sin64(J);
+    ux = fmaf(k, b.x, b.y);
+    uy = fmaf(k, b.y, -b.x);
+  }
+  const float2 a0 = a;
+  a = make_float2(fmaf(f, ux, a0.x), fmaf(f, uy, a0.y));
+  b = make_float2(fmaf(-f, ux, a0.x), fmaf(-f, uy, a0.y));
+}
+
+// Last radix-2 stage of an R-point DFT from the half-size DFTs e (even
+// inputs) and o (odd inputs): v[k] = e[k] + W_R^k o[k], v[k + R/2] =
+// e[k] - W_R^k o[k], unrolled over k by template recursion.
+template <int R, int K = 0>
+struct DftCombine {
+  static __device__ __forceinline__ void run(float2 *v, const float2 *e, const float2 *o) {
+    if constexpr (K < R / 2) {
+      float2 a = e[K], b = o[K];
+      if constexpr (K == 0) {
+        v[K] = cadd(a, b);
+        v[K + R / 2] = csub(a, b);
+      } else if constexpr (4 * K == R) {                 // W = -i
+        const float2 t = make_float2(b.y, -b.x);
+        v[K] = cadd(a, t);
+        v[K + R / 2] = csub(a, t);
+      } else {
+        bfly_tw<K * (64 / R)>(a, b);
+        v[K] = a;
+        v[K + R / 2] = b;
+      }
+      DftCombine<R, K + 1>::run(v, e, o);
+    }
+  }
+};
+
 // In-register forward DFT of size R (R a power of two, R <= 32), natural
 // order in and out: X[k] = sum_n x[n] exp(-2 pi i n k / R).
 template <int R>
@@ -125,20 +189,7 @@ struct Dft {
     }
     Dft<R / 2>::run(e);
     Dft<R / 2>::run(o);
-#pragma unroll
-    for (int k = 0; k < R / 2; ++k) {
-      float2 t;
-      if (k == 0) {
-        t = o[k];
-      } else if (4 * k == R) {            // multiply by -i
-        t = make_float2(o[k].y, -o[k].x);
-      } else {
-        const int j = k * (64 / R);       // angle 2 pi j / 64
-        t = cmul(o[k], make_float2(cos64(j), -sin64(j)));
-      }
-      v[k] = cadd(e[k], t);
-      v[k + R / 2] = csub(e[k], t);
-    }
+    DftCombine<R>::run(v, e, o);
   }
 };
 template <>
