@@ -23,12 +23,18 @@
  *    A larger ldh lets a call use a contiguous run of modes of a wider table
  *    (e.g. modes 3..4 of an order-4 table for the Kronecker workload).
  *  - Limits: 1 <= N <= 8, 1 <= D <= 16, 1 <= J_n, I_n >= 1, every entry of
- *    h for mode n in [0, J_n).  FFT-based calls need Jt <= 16384
- *    (FFT length P = smallest power of two >= Jt, 16 <= P <= 16384);
- *    larger problems return FCS_EUNSUPPORTED.
+ *    h for mode n in [0, J_n).  FFT-based calls (CP route, contractions,
+ *    outer combine) need Jt <= 2^20: the FFT length is P = smallest power of
+ *    two >= Jt, 16 <= P <= 2^20, else FCS_EUNSUPPORTED.  P <= 16384 runs one
+ *    transform per CTA in shared memory; longer transforms use a two-pass
+ *    FFT through the context workspace (at most min(budget, 512 MiB), work
+ *    split into chunks that fit; a few MiB suffice).  fcs_sketch_cp_noalloc
+ *    and the persistent batch kernel take P <= 16384 (batch plans run longer
+ *    problems with their own launches).
  *  - The library allocates only its own context workspace (device memory
- *    reused across calls, bounded by the context's budget) and a 256 KiB
- *    twiddle table.  A context must be used from one host thread at a time.
+ *    reused across calls, bounded by the context's budget), a 256 KiB
+ *    twiddle table and, when enabled, the spectrum cache of fcs_contract.
+ *    A context must be used from one host thread at a time.
  *  - Floating point is FP32 throughout; sums use atomics, so the last bits
  *    of a result may differ from run to run.  Hashes and bins are exact.
  */
@@ -320,6 +326,23 @@ int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
                  const float *fcsT, int64_t B, const float *const *host_vecs,
                  const int32_t *h, const int8_t *s, int64_t ldh,
                  float *out_median, float *out_raw);
+
+/*
+ * fcs_cache_spectra -- enable (1) or disable (0, the default; drops every
+ * entry) the context's cache of sketch spectra for fcs_contract.  When on,
+ * the D half spectra of fcsT that a contraction computes are kept in device
+ * memory outside the workspace (at most 16 entries and min(budget/2, 512 MiB),
+ * least recently used evicted) and reused by later contractions with the
+ * same fcsT pointer, Jt, D and FFT length, which then skip the transform of
+ * the sketch (e.g. the many contractions of one RTPM or ALS loop).  The key
+ * is the pointer: the library's own sketch calls drop the entries of the
+ * buffers they write; after changing a cached sketch any other way, or
+ * before freeing it, call fcs_forget.
+ */
+int fcs_cache_spectra(fcs_ctx *ctx, int enable);
+
+/* fcs_forget -- drop the cached spectra of the sketch at ptr (no-op if none). */
+int fcs_forget(fcs_ctx *ctx, const void *ptr);
 
 /*
  * fcs_recover -- entry estimates from sketches, the decompressing rule of the

@@ -77,6 +77,8 @@ def lib() -> C.CDLL:
                                                     C.POINTER(C.c_void_p), i64p,
                                                     vp, vp, vp, C.c_int64, vp,
                                                     C.c_char_p, C.c_size_t]),
+                "fcs_cache_spectra": (C.c_int, [vp, C.c_int]),
+                "fcs_forget": (C.c_int, [vp, vp]),
                 "fcs_contract": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, i64p,
                                            i32p, C.c_int, vp, C.c_int64,
                                            C.POINTER(C.c_void_p), vp, vp,
@@ -169,7 +171,8 @@ def exported_symbols():
     return ["fcs_version", "fcs_create", "fcs_destroy", "fcs_set_stream",
             "fcs_last_error", "fcs_workspace_bytes", "fcs_make_hashes",
             "fcs_sketch_dense", "fcs_sketch_cp", "fcs_sketch_cp_noalloc",
-            "fcs_contract", "fcs_recover", "fcs_sketch_outer",
+            "fcs_contract", "fcs_cache_spectra", "fcs_forget",
+            "fcs_recover", "fcs_sketch_outer",
             "fcs_batch_plan_create", "fcs_batch_plan_launch",
             "fcs_batch_plan_destroy", "fcs_batch_sketch_cp", "fcs_batch_autotune",
             "fcs_server_create", "fcs_server_destroy", "fcs_server_submit",
@@ -363,6 +366,19 @@ def fcs_sketch_cp_noalloc(U, lam, J, h, s, ldh: int = 0,
     if rc != FCS_OK:
         raise FcsError(rc, err.value.decode(errors="replace"))
     return out
+
+
+def fcs_cache_spectra(ctx: Context, enable: bool = True):
+    """Turn the context's cache of sketch spectra for fcs_contract on or off
+    (off drops every entry).  Cached entries are keyed by the sketch's data
+    pointer: call fcs_forget before changing or freeing a cached sketch."""
+    ctx.check(lib().fcs_cache_spectra(ctx.handle, 1 if enable else 0))
+
+
+def fcs_forget(ctx: Context, sketch):
+    """Drop the cached spectra of `sketch` (a tensor or a device address)."""
+    p = sketch.data_ptr() if isinstance(sketch, torch.Tensor) else int(sketch)
+    ctx.check(lib().fcs_forget(ctx.handle, C.c_void_p(p)))
 
 
 def fcs_contract(ctx: Context, kind: int, fcsT: torch.Tensor, vecs, I, J, h, s,

@@ -44,6 +44,8 @@ struct fcs_batch_plan {
   size_t bytes = 0;
   fcs::BatchBuild build{};
   fcs_ctx *owner = nullptr;
+  std::vector<std::pair<const void *, size_t>> outs;   // output sketches written
+  std::vector<fcs_cp_problem> longp;   // problems with P > 16384: their own launches
 };
 
 namespace fcs {
@@ -314,6 +316,7 @@ struct HostProb {
   Modes m;
   int L, sb;
   int64_t R, utlen, Imax;
+  bool longp;                  // P > 16384: not for the persistent kernel
 };
 
 int check_problem(fcs_ctx *ctx, int k, const fcs_cp_problem &q, HostProb *hp) {
@@ -332,9 +335,10 @@ int check_problem(fcs_ctx *ctx, int k, const fcs_cp_problem &q, HostProb *hp) {
   }
   int log2p = ilog2_ceil(hp->m.Jt);
   if (log2p < kMinLog2P) log2p = kMinLog2P;
-  if (log2p > kMaxLog2P)
+  if (log2p > kMaxLog2PBig)
     return set_error(ctx, FCS_EUNSUPPORTED, "problem %d: Jt=%lld needs FFT length > %d", k,
-                     (long long)hp->m.Jt, 1 << kMaxLog2P);
+                     (long long)hp->m.Jt, 1 << kMaxLog2PBig);
+  hp->longp = log2p > kMaxLog2P;
   hp->L = log2p - 1;
   hp->sb = int((jmax + 3) / 4 * 4);
   hp->R = q.R;
@@ -410,6 +414,10 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
   for (int k = 0; k < nprob; ++k) {
     int rc = check_problem(ctx, k, q[k], &hp[k]);
     if (rc) return rc;
+    if (hp[k].longp)
+      return set_error(ctx, FCS_EUNSUPPORTED,
+                       "problem %d: FFT length > %d is not run by the persistent kernel", k,
+                       1 << kMaxLog2P);
   }
   std::vector<int4> items;
   std::vector<BatchProb> probs(nprob);
@@ -543,12 +551,23 @@ namespace {
 
 // Build a plan: lay the batch out in plan-owned device memory and upload the
 // descriptors.
-int plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain,
+int plan_create(fcs_ctx *ctx, int nprob_all, const fcs_cp_problem *q_all, int grain,
                 fcs_batch_plan **out) {
   *out = nullptr;
+  // problems with P > 16384 run after the persistent kernel, each with the
+  // multi-kernel long-FFT route
+  std::vector<fcs_cp_problem> shortp, longp;
+  for (int k = 0; k < nprob_all; ++k) {
+    HostProb hp{};
+    int rc = check_problem(ctx, k, q_all[k], &hp);
+    if (rc) return rc;
+    (hp.longp ? longp : shortp).push_back(q_all[k]);
+  }
+  const int nprob = int(shortp.size());
+  const fcs_cp_problem *q = shortp.data();
   BatchBuild bb{};
   std::vector<char> desc;
-  int rc = batch_build(ctx, nprob, q, grain, nullptr, &desc, &bb);
+  int rc = nprob ? batch_build(ctx, nprob, q, grain, nullptr, &desc, &bb) : FCS_OK;
   if (rc) return rc;
   if (ctx->ws_bytes + ctx->plan_bytes + bb.total > ctx->budget)
     return set_error(ctx, FCS_ENOMEM_BUDGET,
@@ -556,24 +575,33 @@ int plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain,
                      ctx->budget);
   fcs_batch_plan *plan = new (std::nothrow) fcs_batch_plan();
   if (!plan) return set_error(ctx, FCS_ENOMEM_BUDGET, "out of host memory");
-  cudaError_t e = cudaMalloc(&plan->dev, bb.total);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    delete plan;
-    return check_cuda(ctx, e, "cudaMalloc(batch plan)");
-  }
-  rc = batch_build(ctx, nprob, q, grain, static_cast<char *>(plan->dev), &desc, &bb);
-  if (rc == FCS_OK)
-    rc = check_cuda(ctx, cudaMemcpy(plan->dev, desc.data(), desc.size(), cudaMemcpyHostToDevice),
-                    "cudaMemcpy(batch descriptors)");
-  if (rc) {
-    cudaFree(plan->dev);
-    delete plan;
-    return rc;
+  if (nprob) {
+    cudaError_t e = cudaMalloc(&plan->dev, bb.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete plan;
+      return check_cuda(ctx, e, "cudaMalloc(batch plan)");
+    }
+    rc = batch_build(ctx, nprob, q, grain, static_cast<char *>(plan->dev), &desc, &bb);
+    if (rc == FCS_OK)
+      rc = check_cuda(ctx,
+                      cudaMemcpy(plan->dev, desc.data(), desc.size(), cudaMemcpyHostToDevice),
+                      "cudaMemcpy(batch descriptors)");
+    if (rc) {
+      cudaFree(plan->dev);
+      delete plan;
+      return rc;
+    }
   }
   plan->bytes = bb.total;
   plan->device = ctx->device;
   plan->owner = ctx;
+  plan->longp = longp;
+  for (int k = 0; k < nprob_all; ++k) {
+    int64_t jt = 1;
+    for (int n = 0; n < q_all[k].N; ++n) jt += int64_t(q_all[k].J[n]) - 1;
+    plan->outs.emplace_back(q_all[k].out, sizeof(float) * size_t(q_all[k].D) * size_t(jt));
+  }
   plan->build = bb;
   ctx->plan_bytes += bb.total;
   *out = plan;
@@ -582,7 +610,18 @@ int plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain,
 
 // Device work only: capturable into a CUDA graph.
 int plan_launch(fcs_ctx *ctx, const fcs_batch_plan *plan) {
-  return batch_issue(ctx, static_cast<char *>(plan->dev), plan->build);
+  if (ctx->spec_cache)
+    for (const auto &o : plan->outs) spec_cache_invalidate(ctx, o.first, o.second);
+  if (plan->dev) {
+    int rc = batch_issue(ctx, static_cast<char *>(plan->dev), plan->build);
+    if (rc) return rc;
+  }
+  for (const fcs_cp_problem &p : plan->longp) {
+    int rc = fcs_sketch_cp(ctx, p.N, p.I, p.J, p.R, p.D, p.U, p.ldU, p.lambda, p.h, p.s, p.ldh,
+                           p.out);
+    if (rc) return rc;
+  }
+  return FCS_OK;
 }
 
 void plan_free(fcs_batch_plan *plan) {

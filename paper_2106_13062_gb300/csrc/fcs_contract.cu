@@ -14,10 +14,94 @@
 // (batch item, sketch) that builds each needed Count Sketch in shared memory,
 // transforms it and folds it into the per-thread spectrum product, then either
 // reduces the Parseval sum or runs the inverse FFT and gathers; (3) the median.
+//
+// With fcs_cache_spectra enabled, the spectra of (1) are kept in a
+// per-context cache keyed by the sketch pointer and shape, so repeated
+// contractions against one sketch (the RTPM and ALS loops) transform it
+// once.  fcs_forget drops an entry; the library's own sketch calls drop the
+// entries of the buffers they overwrite.
+#include <vector>
+
 #include "fcs_fft.cuh"
+
+struct fcs_spec_cache {
+  struct Entry {
+    const float *key;
+    int64_t Jt;
+    int D;
+    int log2m;
+    float2 *spec;
+    size_t bytes;
+    cudaEvent_t ready;   // spectrum written
+    cudaEvent_t used;    // last contraction that read it
+    uint64_t tick;
+  };
+  std::vector<Entry> e;
+  size_t bytes = 0;
+  uint64_t tick = 0;
+};
 
 namespace fcs {
 namespace {
+
+constexpr int kSpecCacheEntries = 16;
+constexpr size_t kSpecCacheMaxBytes = size_t(512) << 20;
+
+void spec_entry_free(fcs_spec_cache::Entry &x) {
+  cudaEventSynchronize(x.used);
+  cudaEventDestroy(x.ready);
+  cudaEventDestroy(x.used);
+  cudaFree(x.spec);
+}
+
+void spec_cache_erase(fcs_spec_cache *c, size_t i) {
+  spec_entry_free(c->e[i]);
+  c->bytes -= c->e[i].bytes;
+  c->e.erase(c->e.begin() + i);
+}
+
+// Entry for (key, Jt, D, log2m): an existing one (hit = true) or a new one
+// whose spectrum the caller must compute; nullptr when it cannot be cached.
+fcs_spec_cache::Entry *spec_cache_get(fcs_ctx *ctx, const float *key, int64_t Jt, int D,
+                                      int log2m, bool *hit) {
+  *hit = false;
+  if (!ctx->cache_spectra) return nullptr;
+  if (!ctx->spec_cache) ctx->spec_cache = new (std::nothrow) fcs_spec_cache();
+  fcs_spec_cache *c = ctx->spec_cache;
+  if (!c) return nullptr;
+  ++c->tick;
+  for (auto &x : c->e) {
+    if (x.key == key && x.Jt == Jt && x.D == D && x.log2m == log2m) {
+      x.tick = c->tick;
+      *hit = true;
+      return &x;
+    }
+  }
+  const size_t bytes = sizeof(float2) * size_t(D) * ((size_t(1) << log2m) + 1);
+  const size_t cap = ctx->budget / 2 < kSpecCacheMaxBytes ? ctx->budget / 2 : kSpecCacheMaxBytes;
+  if (bytes > cap) return nullptr;
+  while (!c->e.empty() && (c->bytes + bytes > cap || int(c->e.size()) >= kSpecCacheEntries)) {
+    size_t lru = 0;
+    for (size_t i = 1; i < c->e.size(); ++i)
+      if (c->e[i].tick < c->e[lru].tick) lru = i;
+    spec_cache_erase(c, lru);
+  }
+  fcs_spec_cache::Entry x{key, Jt, D, log2m, nullptr, bytes, nullptr, nullptr, c->tick};
+  if (cudaMalloc(&x.spec, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (cudaEventCreateWithFlags(&x.ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x.used, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (x.ready) cudaEventDestroy(x.ready);
+    cudaFree(x.spec);
+    return nullptr;
+  }
+  c->e.push_back(x);
+  c->bytes += bytes;
+  return &c->e.back();
+}
 
 struct ContractArgs {
   Modes m;
@@ -201,7 +285,8 @@ __global__ void median_kernel(const float *__restrict__ raw, int64_t B, int64_t 
 }
 
 template <int LOG2M>
-int launch_contract(fcs_ctx *ctx, ContractArgs &a, int64_t Jt) {
+int launch_contract(fcs_ctx *ctx, ContractArgs &a, int64_t Jt, bool need_spec,
+                    cudaEvent_t spec_ready) {
   constexpr int NT = fft_threads(LOG2M);
   const int sb_spec = int((Jt + 3) / 4 * 4);
   const size_t smem1 = FftSmem<LOG2M>::bytes(sb_spec);
@@ -214,9 +299,15 @@ int launch_contract(fcs_ctx *ctx, ContractArgs &a, int64_t Jt) {
   if (e == cudaSuccess && smem2 > 48 * 1024)
     e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem2));
   if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(contract)");
-  k1<<<a.D, NT, smem1, ctx->stream>>>(a.fcsT, Jt, Jt, sb_spec, a.spec, ctx->twiddle);
-  int rc = check_cuda(ctx, cudaGetLastError(), "spectrum_kernel");
-  if (rc) return rc;
+  if (need_spec) {
+    k1<<<a.D, NT, smem1, ctx->stream>>>(a.fcsT, Jt, Jt, sb_spec, a.spec, ctx->twiddle);
+    int rc = check_cuda(ctx, cudaGetLastError(), "spectrum_kernel");
+    if (rc) return rc;
+    if (spec_ready) {
+      rc = check_cuda(ctx, cudaEventRecord(spec_ready, ctx->stream), "cudaEventRecord");
+      if (rc) return rc;
+    }
+  }
   k2<<<dim3(unsigned(a.B), unsigned(a.D)), NT, smem2, ctx->stream>>>(a, ctx->twiddle);
   return check_cuda(ctx, cudaGetLastError(), "contract_kernel");
 }
@@ -242,9 +333,48 @@ int launch_median(fcs_ctx *ctx, int D, const float *raw, int64_t B, int64_t widt
 }
 
 }  // namespace
+
+void spec_cache_invalidate(fcs_ctx *ctx, const void *p, size_t bytes) {
+  fcs_spec_cache *c = ctx ? ctx->spec_cache : nullptr;
+  if (!c) return;
+  const char *lo = static_cast<const char *>(p);
+  for (size_t i = c->e.size(); i-- > 0;) {
+    const char *k = reinterpret_cast<const char *>(c->e[i].key);
+    if (k >= lo && k < lo + bytes) spec_cache_erase(c, i);
+  }
+}
+
+void spec_cache_destroy(fcs_ctx *ctx) {
+  fcs_spec_cache *c = ctx->spec_cache;
+  if (!c) return;
+  while (!c->e.empty()) spec_cache_erase(c, c->e.size() - 1);
+  delete c;
+  ctx->spec_cache = nullptr;
+}
+
 }  // namespace fcs
 
 using namespace fcs;
+
+extern "C" int fcs_cache_spectra(fcs_ctx *ctx, int enable) {
+  if (!ctx) return FCS_EINVAL;
+  ctx->err.clear();
+  DeviceGuard g(ctx->device);
+  if (!enable) spec_cache_destroy(ctx);
+  ctx->cache_spectra = enable != 0;
+  return FCS_OK;
+}
+
+extern "C" int fcs_forget(fcs_ctx *ctx, const void *ptr) {
+  if (!ctx) return FCS_EINVAL;
+  ctx->err.clear();
+  fcs_spec_cache *c = ctx->spec_cache;
+  if (!c || !ptr) return FCS_OK;
+  DeviceGuard g(ctx->device);
+  for (size_t i = c->e.size(); i-- > 0;)
+    if (c->e[i].key == ptr) spec_cache_erase(c, i);
+  return FCS_OK;
+}
 
 extern "C" int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
                             const int64_t *host_I, const int32_t *host_J, int D,
@@ -273,11 +403,11 @@ extern "C" int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
     a.vec[n] = host_vecs[n];
   }
   const int log2p = ilog2_ceil(a.m.Jt) < kMinLog2P ? kMinLog2P : ilog2_ceil(a.m.Jt);
-  if (log2p > kMaxLog2P)
+  if (log2p > kMaxLog2PBig)
     return set_error(ctx, FCS_EUNSUPPORTED, "Jt=%lld needs FFT length > %d",
-                     (long long)a.m.Jt, 1 << kMaxLog2P);
+                     (long long)a.m.Jt, 1 << kMaxLog2PBig);
   const int log2m = log2p - 1;
-  const int M = 1 << log2m;
+  const int64_t M = int64_t(1) << log2m;
   a.D = D;
   a.kind = kind;
   a.free_mode = free_mode;
@@ -292,16 +422,48 @@ extern "C" int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
     a.sb = int((jmax + 3) / 4 * 4);
   }
   const int64_t width = kind == FCS_CONTRACT_ALL ? 1 : host_I[free_mode];
-  const size_t sbytes = (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
-  const size_t rbytes = out_raw ? 0 : sizeof(float) * size_t(B) * D * size_t(width);
-  void *ws = nullptr;
-  rc = ensure_workspace(ctx, sbytes + rbytes, &ws);
-  if (rc) return rc;
-  a.spec = static_cast<float2 *>(ws);
-  a.raw = out_raw ? out_raw : reinterpret_cast<float *>(static_cast<char *>(ws) + sbytes);
   DeviceGuard g(ctx->device);
+  bool hit = false;
+  fcs_spec_cache::Entry *ent = spec_cache_get(ctx, fcsT, a.m.Jt, D, log2m, &hit);
+  // the long-FFT path places its own spectrum buffer in the workspace; its
+  // raw buffer must then come from a separate allocation owned by the context
+  const bool big = log2p > kMaxLog2P;
+  const size_t sbytes =
+      (ent || big) ? 0 : (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
+  const size_t rbytes = out_raw ? 0 : sizeof(float) * size_t(B) * D * size_t(width);
+  if (big && rbytes) {
+    rc = ensure_raw(ctx, rbytes);
+    if (rc) return rc;
+  }
+  void *ws = nullptr;
+  if (!big && sbytes + rbytes > 0) {
+    rc = ensure_workspace(ctx, sbytes + rbytes, &ws);
+    if (rc) return rc;
+  }
+  a.spec = ent ? ent->spec : static_cast<float2 *>(ws);
+  a.raw = out_raw ? out_raw
+                  : big ? ctx->raw
+                        : reinterpret_cast<float *>(static_cast<char *>(ws) + sbytes);
+  if (hit) {
+    // the spectrum may have been written on another stream
+    rc = check_cuda(ctx, cudaStreamWaitEvent(ctx->stream, ent->ready, 0), "cudaStreamWaitEvent");
+    if (rc) return rc;
+  }
   rc = FCS_EUNSUPPORTED;
-  FCS_DISPATCH_LOG2M(log2m, rc = launch_contract<L>(ctx, a, a.m.Jt));
-  if (rc) return rc;
+  if (log2p > kMaxLog2P) {
+    rc = big_contract(ctx, a.m, kind, free_mode, D, fcsT, B, a.vec, h, s, ent ? ent->spec : nullptr,
+                      !hit, ent ? ent->ready : nullptr, a.raw, log2p);
+  } else {
+    FCS_DISPATCH_LOG2M(log2m, rc = launch_contract<L>(ctx, a, a.m.Jt, !hit,
+                                                      ent ? ent->ready : nullptr));
+  }
+  if (rc) {
+    if (ent && !hit) fcs_forget(ctx, fcsT);      // never computed
+    return rc;
+  }
+  if (ent) {
+    rc = check_cuda(ctx, cudaEventRecord(ent->used, ctx->stream), "cudaEventRecord");
+    if (rc) return rc;
+  }
   return launch_median(ctx, D, a.raw, B, width, out_median);
 }

@@ -519,9 +519,14 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
       return set_error(ctx, FCS_EINVAL, "ldU[%d]=%lld < R", n, (long long)host_ldU[n]);
   }
   const int log2p = ilog2_ceil(a.m.Jt) < kMinLog2P ? kMinLog2P : ilog2_ceil(a.m.Jt);
-  if (log2p > kMaxLog2P)
+  if (log2p > kMaxLog2PBig)
     return set_error(ctx, FCS_EUNSUPPORTED, "Jt=%lld needs FFT length > %d",
-                     (long long)a.m.Jt, 1 << kMaxLog2P);
+                     (long long)a.m.Jt, 1 << kMaxLog2PBig);
+  if (log2p > kMaxLog2P) {
+    DeviceGuard g(ctx->device);
+    spec_cache_invalidate(ctx, out, sizeof(float) * size_t(D) * size_t(a.m.Jt));
+    return big_sketch_cp(ctx, a.m, R, D, host_U, host_ldU, lambda, h, s, out, log2p);
+  }
   const int log2m = log2p - 1;
   const int M = 1 << log2m;
   a.D = D;
@@ -554,6 +559,7 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
   float *UT = reinterpret_cast<float *>(static_cast<char *>(ws) + gbytes + cbytes);
   a.UT = UT;
   DeviceGuard g(ctx->device);
+  spec_cache_invalidate(ctx, out, sizeof(float) * size_t(D) * size_t(a.m.Jt));
   rc = check_cuda(ctx, cudaMemsetAsync(ws, 0, gbytes + cbytes, ctx->stream),
                   "cudaMemsetAsync(cp workspace)");
   if (rc) return rc;

@@ -53,6 +53,29 @@ int ensure_workspace(fcs_ctx *ctx, size_t bytes, void **out) {
   return FCS_OK;
 }
 
+int ensure_raw(fcs_ctx *ctx, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes <= ctx->raw_bytes) return FCS_OK;
+  if (bytes > ctx->budget)
+    return set_error(ctx, FCS_ENOMEM_BUDGET, "buffer of %zu bytes exceeds the context budget",
+                     bytes);
+  if (ctx->raw) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaStreamSynchronize");
+    cudaFree(ctx->raw);
+    ctx->raw = nullptr;
+    ctx->raw_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&ctx->raw, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->raw = nullptr;
+    return check_cuda(ctx, e, "cudaMalloc(raw)");
+  }
+  ctx->raw_bytes = bytes;
+  return FCS_OK;
+}
+
 int make_modes(fcs_ctx *ctx, int N, const int64_t *host_I, const int32_t *host_J,
                int64_t ldh, Modes *m) {
   if (N < 1 || N > kMaxN) return set_error(ctx, FCS_EINVAL, "N=%d outside [1,%d]", N, kMaxN);
@@ -143,7 +166,9 @@ extern "C" int fcs_destroy(fcs_ctx *ctx) {
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   batch_state_destroy(ctx);
+  spec_cache_destroy(ctx);
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->raw) cudaFree(ctx->raw);
   if (ctx->twiddle) cudaFree(ctx->twiddle);
   delete ctx;
   return FCS_OK;

@@ -312,6 +312,7 @@ extern "C" int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
   const bool use_smem = smem <= 200 * 1024;
 
   DeviceGuard g(ctx->device);
+  spec_cache_invalidate(ctx, out, sizeof(float) * size_t((nbatch - 1) * a.obs + D * Jt));
   // zero the output sketches
   {
     int64_t len = D * Jt;

@@ -32,6 +32,10 @@ struct fcs_ctx {
   size_t ws_bytes = 0;
   size_t plan_bytes = 0;         // device bytes held by live batch plans
   struct fcs_batch_state *batch = nullptr;   // autotune cache (fcs_batch.cu)
+  struct fcs_spec_cache *spec_cache = nullptr;   // sketch spectra (fcs_contract.cu)
+  bool cache_spectra = false;                    // fcs_cache_spectra
+  float *raw = nullptr;          // per-sketch estimates of long contractions
+  size_t raw_bytes = 0;
   std::string err;
 };
 
@@ -41,14 +45,21 @@ constexpr int kLogTwN = 15;            // twiddle table resolution 2^15
 constexpr int kTwN = 1 << kLogTwN;
 constexpr int kMaxN = 8;
 constexpr int kMaxD = 16;
-constexpr int kMaxLog2P = 14;          // FFT length P <= 16384
+constexpr int kMaxLog2P = 14;          // FFT length P <= 16384 in one CTA
+constexpr int kMaxLog2PBig = 20;       // longer transforms through global memory
 constexpr int kMinLog2P = 4;
 
 int set_error(fcs_ctx *ctx, int code, const char *fmt, ...);
 void batch_state_destroy(fcs_ctx *ctx);
+// Spectrum cache of fcs_contract: drop the entries whose key lies in
+// [p, p + bytes) (after the work that still reads them), or all of them.
+void spec_cache_invalidate(fcs_ctx *ctx, const void *p, size_t bytes);
+void spec_cache_destroy(fcs_ctx *ctx);
 int check_cuda(fcs_ctx *ctx, cudaError_t e, const char *what);
 // Grow the workspace to at least `bytes` (contents are not preserved).
 int ensure_workspace(fcs_ctx *ctx, size_t bytes, void **out);
+// Grow ctx->raw to at least `bytes` (counted against the budget with the workspace).
+int ensure_raw(fcs_ctx *ctx, size_t bytes);
 
 // RAII guard that makes ctx->device current for the duration of a call.
 struct DeviceGuard {
@@ -455,5 +466,17 @@ struct Modes {
 
 int make_modes(fcs_ctx *ctx, int N, const int64_t *host_I, const int32_t *host_J,
                int64_t ldh, Modes *m);
+
+// FFT-based calls for kMaxLog2P < log2p <= kMaxLog2PBig (fcs_big.cu); the
+// callers have validated the arguments.
+int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *const *host_U,
+                  const int64_t *host_ldU, const float *lambda, const int32_t *h,
+                  const int8_t *s, float *out, int log2p);
+int big_contract(fcs_ctx *ctx, const Modes &m, int kind, int free_mode, int D,
+                 const float *fcsT, int64_t B, const float *const *vec, const int32_t *h,
+                 const int8_t *s, float2 *spec, bool need_spec, cudaEvent_t spec_ready,
+                 float *raw, int log2p);
+int big_outer(fcs_ctx *ctx, int64_t nbatch, int D, int64_t La, int64_t Lb, const float *fa,
+              const float *fb, float *out, int log2p);
 
 }  // namespace fcs

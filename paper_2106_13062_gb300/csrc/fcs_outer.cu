@@ -88,10 +88,12 @@ extern "C" int fcs_sketch_outer(fcs_ctx *ctx, int64_t nbatch, int D, int64_t La,
   if (!fa || !fb || !out) return set_error(ctx, FCS_EINVAL, "NULL pointer argument");
   const int64_t Lo = La + Lb - 1;
   const int log2p = ilog2_ceil(Lo) < kMinLog2P ? kMinLog2P : ilog2_ceil(Lo);
-  if (log2p > kMaxLog2P)
+  if (log2p > kMaxLog2PBig)
     return set_error(ctx, FCS_EUNSUPPORTED, "output length %lld needs FFT length > %d",
-                     (long long)Lo, 1 << kMaxLog2P);
+                     (long long)Lo, 1 << kMaxLog2PBig);
   DeviceGuard g(ctx->device);
+  spec_cache_invalidate(ctx, out, sizeof(float) * size_t(nbatch) * D * size_t(Lo));
+  if (log2p > kMaxLog2P) return big_outer(ctx, nbatch, D, La, Lb, fa, fb, out, log2p);
   int rc = FCS_EUNSUPPORTED;
   FCS_DISPATCH_LOG2M(log2p - 1, rc = launch_outer<L>(ctx, nbatch, D, La, Lb, fa, fb, out));
   return rc;

@@ -374,7 +374,14 @@ int issue_round(fcs_server *S, int si, std::vector<Req *> &reqs, Round &rd) {
       p.s = q->ds;
       p.ldh = 0;
       p.out = q->dout;
-      probs.push_back(p);
+      if (q->Jt > (int64_t(1) << fcs::kMaxLog2P)) {
+        // too long for the persistent kernel: its own (multi-kernel) launch
+        rc = fcs_sketch_cp(ctx, p.N, p.I, p.J, p.R, p.D, p.U, p.ldU, p.lambda, p.h, p.s, p.ldh,
+                           p.out);
+        if (rc) return rc;
+      } else {
+        probs.push_back(p);
+      }
       cps.push_back(q);
     } else {
       for (int n = 0; n < r.N; ++n) {
@@ -533,7 +540,7 @@ int validate(const fcs_server *S, const fcs_request &r) {
     if (!r.host_out && !r.keep_resident) return FCS_EINVAL;
     int l = 0;
     while ((int64_t(1) << l) < jtilde_of(r.N, r.J)) ++l;
-    if (l > 14) return FCS_EUNSUPPORTED;
+    if (l > fcs::kMaxLog2PBig) return FCS_EUNSUPPORTED;
   } else {
     if (r.B < 1 || r.B > 65535 || !r.host_result) return FCS_EINVAL;
     if (r.contract_kind != FCS_CONTRACT_ALL && r.contract_kind != FCS_CONTRACT_FREE)

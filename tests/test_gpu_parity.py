@@ -408,8 +408,8 @@ def test_argument_errors(fcs, ctx):
         fcs.fcs_make_hashes(ctx, 1, [10, 0], [5, 5], 1)
     assert e.value.code == fcs.FCS_EINVAL
     U = [torch.randn(10, 3, device="cuda") for _ in range(2)]
-    with pytest.raises(fcs.FcsError) as e:
-        fcs.fcs_sketch_cp(ctx, U, None, [9000, 9000], h, s)
+    with pytest.raises(fcs.FcsError) as e:        # Jt > 2^20
+        fcs.fcs_sketch_cp(ctx, U, None, [600000, 600000], h, s)
     assert e.value.code == fcs.FCS_EUNSUPPORTED
     with pytest.raises(ValueError):          # the binding checks the table stride
         fcs.fcs_sketch_dense(ctx, torch.randn(10, 10, device="cuda"), [5, 5], h, s,
