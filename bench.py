@@ -520,19 +520,27 @@ class KronWorkload:
 
 def mixed_cp_shapes(seed: int, count: int):
     """Heterogeneous CP problems: order 3 or 4, I_n log-uniform in [50, 2000],
-    rank log-uniform in [1, 256], J_n log-uniform in [256, 8192] capped so that
-    Jt <= 16384, D uniform in 1..10."""
+    rank log-uniform in [1, 256], J_n log-uniform in [256, 8192] (so Jt up to
+    32765 and FFT lengths up to 32768), D uniform in 1..10."""
     g = np.random.default_rng(seed)
     shapes = []
     for _ in range(count):
         N = int(g.integers(3, 5))
         I = [int(round(math.exp(g.uniform(math.log(50), math.log(2000))))) for _ in range(N)]
         R = int(round(math.exp(g.uniform(0.0, math.log(256)))))
-        jmax = min(8192, (16384 + N - 1) // N)
-        J = [int(round(math.exp(g.uniform(math.log(256), math.log(jmax))))) for _ in range(N)]
+        J = [int(round(math.exp(g.uniform(math.log(256), math.log(8192))))) for _ in range(N)]
         D = int(g.integers(1, 11))
         shapes.append((I, J, max(1, R), D))
     return shapes
+
+
+def long_cp_launches(J) -> int:
+    """Kernels of one CP-route sketch with P > 16384 (two-pass FFT route):
+    Count Sketches, pass 1, [pass 2,] accumulate per chunk of transforms, then
+    pack, pass 1, [pass 2,] unpack for the inverse (one chunk here)."""
+    P = fft_len(jt_of(J))
+    p2 = 1 if P > 32768 else 0
+    return (3 + p2) + (3 + p2)
 
 
 class BatchWorkload:
@@ -549,14 +557,18 @@ class BatchWorkload:
     def config(self):
         return {"workload": self.name, "problems": self.count,
                 "order": "3-4", "I": "log-U[50,2000]", "R": "log-U[1,256]",
-                "J": "log-U[256,8192], Jt<=16384", "D": "U{1..10}",
+                "J": "log-U[256,8192] (Jt up to 32765, P up to 32768)", "D": "U{1..10}",
+                "long_problems": sum(1 for _, J, _, _ in self.shapes if fft_len(jt_of(J)) > 16384),
                 "sketches_per_step": self.sketches_per_step(), "seed": self.seed}
 
     def sketches_per_step(self):
         return sum(D for _, _, _, D in self.shapes)
 
     def launches_per_step(self):
-        return 2                      # batched transpose + persistent kernel
+        # batched transpose + persistent kernel; problems with P > 16384 run
+        # on the two-pass long-FFT route after it
+        return 2 + sum(long_cp_launches(J) for _, J, _, _ in self.shapes
+                       if fft_len(jt_of(J)) > 16384)
 
     def setup(self, fcs, ctx, dev):
         import torch
@@ -668,7 +680,8 @@ WORKLOADS = {"cp": CpWorkload, "dense": DenseWorkload, "kron": KronWorkload,
 def run_serve(args, rank, world, local_rank):
     """Serving workload: 10,000 requests with Poisson arrivals, half CP-route
     sketches (order 3-4, I_n log-U[50,2000], rank log-U[1,256], J_n
-    log-U[256,8192] with Jt <= 16384, D U{1..10}; 96 shape templates), half
+    log-U[256,8192], so FFT lengths up to 32768, D U{1..10}; 96 shape
+    templates), half
     contractions (T(u,u,u) : T(I,u,u) = 1 : 1, 1-16 vectors) against 16
     resident sketches.  The offered rate is 0.8 x the capacity of the plain
     path (one request at a time: copy in, hashes, one launch, copy out,
@@ -824,7 +837,7 @@ def run_serve(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "serve_10k_poisson_mixed", "requests": nreq,
-                   "mix": "50% CP sketch (96 templates, order 3-4, I log-U[50,2000], R log-U[1,256], J log-U[256,8192], Jt<=16384, D U{1..10}); 50% contractions UUU:IUU 1:1, B U{1..16}, 16 resident sketches",
+                   "mix": "50% CP sketch (96 templates, order 3-4, I log-U[50,2000], R log-U[1,256], J log-U[256,8192] so P up to 32768, D U{1..10}); 50% contractions UUU:IUU 1:1, B U{1..16}, 16 resident sketches",
                    "arrivals": "Poisson, rate 0.8 x measured plain capacity", "seed": 7,
                    "server": "4 streams, 128 slots, 48 CP per round"},
         "serving": {

@@ -16,6 +16,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import threading
+import weakref
 
 import torch
 
@@ -240,6 +241,7 @@ class Context:
         if rc != FCS_OK:
             raise FcsError(rc, "fcs_create failed")
         self._h = h
+        self._plans = weakref.WeakSet()      # batch plans, closed before the context
 
     @property
     def handle(self):
@@ -259,6 +261,8 @@ class Context:
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
+            for p in list(getattr(self, "_plans", ())):
+                p.close()
             lib().fcs_destroy(self._h)
             self._h = C.c_void_p()
 
@@ -526,6 +530,7 @@ class BatchPlan:
         ctx.check(lib().fcs_batch_plan_create(ctx.handle, len(problems), self._arr,
                                               grain, C.byref(h)))
         self._h = h
+        ctx._plans.add(self)
 
     def launch(self):
         self.ctx._sync_stream()

@@ -28,6 +28,7 @@
 #include <array>
 #include <cstring>
 #include <map>
+#include <set>
 #include <vector>
 
 #include "fcs_batch_internal.cuh"
@@ -36,6 +37,7 @@
 struct fcs_batch_state {
   std::map<uint64_t, int> tuned;   // batch signature -> grain
   bool cache_loaded = false;
+  std::set<fcs_batch_plan *> plans;   // live plans; detached when the context goes
 };
 
 struct fcs_batch_plan {
@@ -46,6 +48,8 @@ struct fcs_batch_plan {
   fcs_ctx *owner = nullptr;
   std::vector<std::pair<const void *, size_t>> outs;   // output sketches written
   std::vector<fcs_cp_problem> longp;   // problems with P > 16384: their own launches
+  void *long_ws = nullptr;             // their scratch, owned by the plan (graph-safe)
+  size_t long_bytes = 0;
 };
 
 namespace fcs {
@@ -597,13 +601,38 @@ int plan_create(fcs_ctx *ctx, int nprob_all, const fcs_cp_problem *q_all, int gr
   plan->device = ctx->device;
   plan->owner = ctx;
   plan->longp = longp;
+  if (!longp.empty()) {
+    // one scratch buffer for the long problems, run one after another; a
+    // modest cap keeps the plan small (the route works in chunks)
+    size_t room = ctx->budget > ctx->ws_bytes + ctx->plan_bytes + bb.total
+                      ? ctx->budget - (ctx->ws_bytes + ctx->plan_bytes + bb.total)
+                      : 0;
+    const size_t cap = std::min<size_t>(room, size_t(256) << 20);
+    size_t need = 0;
+    for (const fcs_cp_problem &p : longp) {
+      Modes m{};
+      make_modes(ctx, p.N, p.I, p.J, p.ldh, &m);
+      const int log2p = ilog2_ceil(m.Jt);
+      need = std::max(need, big_sketch_cp_bytes(m, p.R, p.D, log2p, cap));
+    }
+    cudaError_t e = need > cap ? cudaErrorMemoryAllocation : cudaMalloc(&plan->long_ws, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (plan->dev) cudaFree(plan->dev);
+      delete plan;
+      return set_error(ctx, FCS_ENOMEM_BUDGET, "no room for the long problems' scratch (%zu B)",
+                       need);
+    }
+    plan->long_bytes = need;
+  }
   for (int k = 0; k < nprob_all; ++k) {
     int64_t jt = 1;
     for (int n = 0; n < q_all[k].N; ++n) jt += int64_t(q_all[k].J[n]) - 1;
     plan->outs.emplace_back(q_all[k].out, sizeof(float) * size_t(q_all[k].D) * size_t(jt));
   }
   plan->build = bb;
-  ctx->plan_bytes += bb.total;
+  ctx->plan_bytes += bb.total + plan->long_bytes;
+  ctx->batch->plans.insert(plan);
   *out = plan;
   return FCS_OK;
 }
@@ -617,8 +646,11 @@ int plan_launch(fcs_ctx *ctx, const fcs_batch_plan *plan) {
     if (rc) return rc;
   }
   for (const fcs_cp_problem &p : plan->longp) {
-    int rc = fcs_sketch_cp(ctx, p.N, p.I, p.J, p.R, p.D, p.U, p.ldU, p.lambda, p.h, p.s, p.ldh,
-                           p.out);
+    Modes m{};
+    int rc = make_modes(ctx, p.N, p.I, p.J, p.ldh, &m);
+    if (rc) return rc;
+    rc = big_sketch_cp(ctx, m, p.R, p.D, p.U, p.ldU, p.lambda, p.h, p.s, p.out,
+                       ilog2_ceil(m.Jt), plan->long_ws, plan->long_bytes);
     if (rc) return rc;
   }
   return FCS_OK;
@@ -626,8 +658,12 @@ int plan_launch(fcs_ctx *ctx, const fcs_batch_plan *plan) {
 
 void plan_free(fcs_batch_plan *plan) {
   if (!plan) return;
-  if (plan->owner) plan->owner->plan_bytes -= plan->bytes;
+  if (plan->owner) {
+    plan->owner->plan_bytes -= plan->bytes + plan->long_bytes;
+    if (plan->owner->batch) plan->owner->batch->plans.erase(plan);
+  }
   if (plan->dev) cudaFree(plan->dev);
+  if (plan->long_ws) cudaFree(plan->long_ws);
   delete plan;
 }
 
@@ -648,6 +684,9 @@ using namespace fcs;
 namespace fcs {
 void batch_state_destroy(fcs_ctx *ctx) {
   if (ctx && ctx->batch) {
+    // plans outlive their context only as device memory: a later
+    // fcs_batch_plan_destroy must not touch the context
+    for (fcs_batch_plan *p : ctx->batch->plans) p->owner = nullptr;
     delete ctx->batch;
     ctx->batch = nullptr;
   }
@@ -688,7 +727,10 @@ extern "C" int fcs_batch_plan_launch(fcs_ctx *ctx, const fcs_batch_plan *plan) {
 extern "C" int fcs_batch_plan_destroy(fcs_batch_plan *plan) {
   if (!plan) return FCS_OK;
   DeviceGuard g(plan->device);
-  if (plan->owner) cudaStreamSynchronize(plan->owner->stream);
+  if (plan->owner)
+    cudaStreamSynchronize(plan->owner->stream);
+  else
+    cudaDeviceSynchronize();           // the context is gone: wait for any user of the plan
   plan_free(plan);
   return FCS_OK;
 }

@@ -472,22 +472,53 @@ unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) / per); 
 }  // namespace
 
 // ---------------------------------------------------------------- host routes
-int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *const *host_U,
-                  const int64_t *host_ldU, const float *lambda, const int32_t *h,
-                  const int8_t *s, float *out, int log2p) {
-  const int L1 = log2p - 1 - kL2;
+namespace {
+// Chunk size (transforms) and workspace bytes of the long CP route under `cap`.
+void big_cp_plan(const Modes &m, int64_t R, int D, int log2p, size_t cap, int64_t *tc_out,
+                 size_t *bytes_out) {
   const int64_t M = int64_t(1) << (log2p - 1), P = 2 * M;
   const int N = m.N;
   const size_t gbytes = (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
   const size_t per_t = sizeof(float) * size_t(P) * 2;          // real input + transform
-  const size_t cap = std::min(ctx->budget, kBigWorkspaceCap);
   const int64_t total = int64_t(D) * R * N;
   int64_t tc = cap > gbytes ? int64_t((cap - gbytes) / per_t) : 0;
   tc = std::min(std::max<int64_t>(tc / N * N, N), total);         // whole ranks per chunk
   const int64_t nbuf = std::max<int64_t>(tc, D);                   // D rows for the inverse
-  void *ws = nullptr;
-  int rc = ensure_workspace(ctx, gbytes + per_t * size_t(nbuf), &ws);
-  if (rc) return rc;
+  *tc_out = tc;
+  *bytes_out = gbytes + per_t * size_t(nbuf);
+}
+}  // namespace
+
+size_t big_sketch_cp_bytes(const Modes &m, int64_t R, int D, int log2p, size_t cap) {
+  int64_t tc;
+  size_t bytes;
+  big_cp_plan(m, R, D, log2p, cap, &tc, &bytes);
+  return bytes;
+}
+
+int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *const *host_U,
+                  const int64_t *host_ldU, const float *lambda, const int32_t *h,
+                  const int8_t *s, float *out, int log2p, void *ext_ws, size_t ext_bytes) {
+  const int L1 = log2p - 1 - kL2;
+  const int64_t M = int64_t(1) << (log2p - 1), P = 2 * M;
+  const int N = m.N;
+  const size_t gbytes = (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
+  const int64_t total = int64_t(D) * R * N;
+  int64_t tc;
+  size_t need;
+  big_cp_plan(m, R, D, log2p, ext_ws ? ext_bytes : std::min(ctx->budget, kBigWorkspaceCap),
+              &tc, &need);
+  void *ws = ext_ws;
+  int rc = FCS_OK;
+  if (ws) {
+    if (need > ext_bytes)
+      return set_error(ctx, FCS_ENOMEM_BUDGET, "long CP sketch needs %zu bytes, plan holds %zu",
+                       need, ext_bytes);
+  } else {
+    rc = ensure_workspace(ctx, need, &ws);
+    if (rc) return rc;
+  }
+  const int64_t nbuf = std::max<int64_t>(tc, D);
   float2 *G = static_cast<float2 *>(ws);
   float *xb = reinterpret_cast<float *>(static_cast<char *>(ws) + gbytes);
   float2 *Zb = reinterpret_cast<float2 *>(xb + size_t(nbuf) * P);

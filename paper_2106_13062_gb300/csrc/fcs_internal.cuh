@@ -469,9 +469,14 @@ int make_modes(fcs_ctx *ctx, int N, const int64_t *host_I, const int32_t *host_J
 
 // FFT-based calls for kMaxLog2P < log2p <= kMaxLog2PBig (fcs_big.cu); the
 // callers have validated the arguments.
+// ext_ws: caller-owned device buffer of ext_bytes (a batch plan's), or NULL
+// for the context workspace.
 int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *const *host_U,
                   const int64_t *host_ldU, const float *lambda, const int32_t *h,
-                  const int8_t *s, float *out, int log2p);
+                  const int8_t *s, float *out, int log2p, void *ext_ws = nullptr,
+                  size_t ext_bytes = 0);
+// Device bytes big_sketch_cp uses when its buffer holds at most `cap` bytes.
+size_t big_sketch_cp_bytes(const Modes &m, int64_t R, int D, int log2p, size_t cap);
 int big_contract(fcs_ctx *ctx, const Modes &m, int kind, int free_mode, int D,
                  const float *fcsT, int64_t B, const float *const *vec, const int32_t *h,
                  const int8_t *s, float2 *spec, bool need_spec, cudaEvent_t spec_ready,

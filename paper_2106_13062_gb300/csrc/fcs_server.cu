@@ -274,6 +274,10 @@ std::vector<Req *> admit(fcs_server *S) {
     }
     if (S->inflight >= S->cfg.max_inflight) break;
     if (q->r.kind == FCS_REQ_CP && ncp >= S->cfg.max_batch) break;
+    // a CP request with P > 16384 (multi-kernel long-FFT route) gets a round
+    // of its own, so it does not hold back the completion of short requests
+    const bool longq = q->r.kind == FCS_REQ_CP && q->Jt > (int64_t(1) << fcs::kMaxLog2P);
+    if (longq && !got.empty()) break;
     size_t doff = 0, poff = 0, koff = 0;
     if (!S->darena.alloc(q->dev_bytes, &doff)) break;
     if (!S->parena.alloc(q->pin_bytes, &poff)) {
@@ -309,6 +313,7 @@ std::vector<Req *> admit(fcs_server *S) {
     S->inflight++;
     S->max_inflight_seen = std::max(S->max_inflight_seen, S->inflight);
     got.push_back(q);
+    if (longq) break;
   }
   return got;
 }

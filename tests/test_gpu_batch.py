@@ -132,3 +132,32 @@ def test_batch_rejects_bad_problem(fcs, ctx):
     with pytest.raises(fcs.FcsError) as e:
         fcs.fcs_batch_sketch_cp(ctx, probs)
     assert e.value.code == fcs.FCS_EINVAL
+
+
+def test_plan_outliving_its_context(fcs):
+    """C-ABI order context-destroy-then-plan-destroy: the plan is detached from
+    the context and its destruction must not touch the freed context (a long
+    problem gives the plan its own scratch too)."""
+    import ctypes as C
+    L = fcs.lib()
+    own = fcs.Context()
+    probs, _, keep = _make(fcs, own, seed=7)
+    U, lam = synth.cp_factors(99, [80, 90, 70], 3)
+    Ug, lamg = [cuda(u) for u in U], cuda(lam)
+    h, s = fcs.fcs_make_hashes(own, 98, [80, 90, 70], [9000, 8000, 7000], 2)   # P = 2^15
+    pr, out = fcs.cp_problem(Ug, lamg, [9000, 8000, 7000], h, s)
+    probs.append(pr)
+    arr = fcs._problem_array(probs)
+    ph = C.c_void_p()
+    own.check(L.fcs_batch_plan_create(own.handle, len(probs), arr, 0, C.byref(ph)))
+    own.check(L.fcs_batch_plan_launch(own.handle, ph))
+    torch.cuda.synchronize()
+    assert L.fcs_destroy(own.handle) == fcs.FCS_OK
+    own._h = C.c_void_p()                        # already destroyed above
+    assert L.fcs_batch_plan_destroy(ph) == fcs.FCS_OK
+    # a Python plan closes before its context
+    c2 = fcs.Context()
+    probs2, _, keep2 = _make(fcs, c2, seed=8)
+    plan = fcs.BatchPlan(c2, probs2)
+    c2.close()
+    assert not plan._h.value
