@@ -62,6 +62,8 @@ def _load():
                 "fcso_fcs_dense": (None, [C.c_int, i64p, i64p, i32p, C.c_int,
                                           f64p, i32p, i8p, f64p]),
                 "fcso_long_hash": (None, [C.c_int, i64p, i32p, i8p, i32p, i8p]),
+                "fcso_ts_dense": (None, [C.c_int, i64p, i64p, C.c_int32, C.c_int,
+                                         f64p, i32p, i8p, f64p]),
                 "fcso_cp_to_dense": (None, [C.c_int, i64p, C.c_int64, f64pp,
                                             i64p, f64p, f64p]),
                 "fcso_fcs_cp": (None, [C.c_int, i64p, i32p, C.c_int64, C.c_int,
@@ -184,6 +186,25 @@ def fcs_dense(T, J, h, s, D: int | None = None) -> np.ndarray:
                            _p(J, C.c_int32), D, _p(Tb, C.c_double),
                            _p(h, C.c_int32), _p(s, C.c_int8),
                            _p(out, C.c_double))
+    return out
+
+
+def ts_dense(T, J: int, h, s, D: int | None = None) -> np.ndarray:
+    """Def. 2: Tensor Sketch of T (every hash length J; bins (sum h) mod J).
+    Returns [D, J]."""
+    T = np.asarray(T)
+    I = _i64(T.shape)
+    Tb = T.astype(np.float64, copy=False)
+    if not Tb.flags.c_contiguous and not Tb.flags.f_contiguous:
+        Tb = np.ascontiguousarray(Tb)
+    stride = _i64([st // Tb.itemsize for st in Tb.strides])
+    h = _i32(h)
+    s = _i8(s)
+    D = h.shape[0] if D is None else D
+    out = np.zeros((D, int(J)), dtype=np.float64)
+    _load().fcso_ts_dense(len(I), _p(I, C.c_int64), _p(stride, C.c_int64), int(J), D,
+                          _p(Tb, C.c_double), _p(h, C.c_int32), _p(s, C.c_int8),
+                          _p(out, C.c_double))
     return out
 
 

@@ -162,6 +162,44 @@ void fcso_fcs_dense(int N, const int64_t *I, const int64_t *stride,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Tensor Sketch, Def. 2 (every hash length J):                              */
+/*   TS(T)_j = sum_{H(i_1..i_N)=j} S(i_1..i_N) T(i_1..i_N),                  */
+/*   H = (sum_n h_n(i_n)) mod J (0-based form of the paper's                 */
+/*   (h_1 + ... + h_N - N) mod J + 1),  S = prod_n s_n(i_n).                 */
+/* Same traversal and table layout as fcso_fcs_dense; out: [D][J].           */
+/* ------------------------------------------------------------------------ */
+void fcso_ts_dense(int N, const int64_t *I, const int64_t *stride, int32_t J, int D,
+                   const double *T, const int32_t *h, const int8_t *s, double *out)
+{
+    int64_t total = 0, numel = 1;
+    int64_t off[16];
+    for (int n = 0; n < N; ++n) { off[n] = total; total += I[n]; numel *= I[n]; }
+#pragma omp parallel for schedule(static)
+    for (int d = 0; d < D; ++d) {
+        const int32_t *hd = h + (size_t)d * total;
+        const int8_t *sd = s + (size_t)d * total;
+        double *o = out + (size_t)d * J;
+        for (int64_t j = 0; j < J; ++j) o[j] = 0.0;
+        int64_t idx[16];
+        for (int n = 0; n < N; ++n) idx[n] = 0;
+        for (int64_t e = 0; e < numel; ++e) {
+            int64_t sum = 0, addr = 0;
+            double sign = 1.0;
+            for (int n = 0; n < N; ++n) {
+                sum += hd[off[n] + idx[n]];
+                sign *= (double)sd[off[n] + idx[n]];
+                addr += idx[n] * stride[n];
+            }
+            o[sum % J] += sign * T[addr];
+            for (int n = N - 1; n >= 0; --n) {
+                if (++idx[n] < I[n]) break;
+                idx[n] = 0;
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Long hash pair of Def. 4 for one sketch: for the column-major linear      */
 /* index l = sum_n i_n prod_{m<n} I_m (0-based form of the paper's formula), */
 /*   H(l) = sum_n h_n(i_n),  S(l) = prod_n s_n(i_n).                         */
