@@ -341,8 +341,62 @@ int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
  */
 int fcs_cache_spectra(fcs_ctx *ctx, int enable);
 
-/* fcs_forget -- drop the cached spectra of the sketch at ptr (no-op if none). */
+/* fcs_forget -- invalidate the cached spectra of the sketch at ptr (recomputed
+ * on next use; no-op if none).  Does not wait for the device. */
 int fcs_forget(fcs_ctx *ctx, const void *ptr);
+
+/*
+ * fcs_fold -- Tensor Sketch (Def. 2) from Fast Count Sketch: with every
+ * J_n = J the TS bin (sum_n h_n) mod J is the FCS bin reduced mod J, so
+ *     out[r][j] = sum_{k = j mod J} in[r][k]
+ * turns FCS sketches into the TS sketches with the same hash functions (the
+ * comparison of Prop. 1).  in [nrows][Jt], out [nrows][J], rows contiguous;
+ * 1 <= nrows <= 65535.
+ */
+int fcs_fold(fcs_ctx *ctx, int64_t nrows, int64_t Jt, const float *in, int64_t J, float *out);
+
+/*
+ * fcs_sketch_inner -- the compressed tensor regression layer (TRL
+ * subsection, eq. net_compress): with the activation sketches sa
+ * [B][D][Jt] (FCS_d of each input X_b) and weight sketches sw [C][D][Jt]
+ * (FCS_d of each class's weight tensor W_c), all with the same hashes,
+ *     raw[b][c][d] = < sa[b][d], sw[c][d] >,
+ *     out_median[b][c] = median_d raw[b][c][d] + bias[c].
+ * bias NULL or [C]; out_raw NULL or [B][C][D].  B <= 4194240.
+ */
+int fcs_sketch_inner(fcs_ctx *ctx, int D, int64_t Jt, int64_t B, const float *sa, int64_t C,
+                     const float *sw, const float *bias, float *out_median, float *out_raw);
+
+/*
+ * fcs_rtpm -- sketched robust tensor power method (RTPM subsection) for a
+ * symmetric order-N tensor of dimension I, from its sketches fcsT [D][Jt]
+ * (hash tables h, s, ldh; every J_n from host_J[0..N)): for each of K
+ * components, L starting vectors init[k][l][:] (normalised by the call),
+ * n_iter power iterations u <- T(I,u,..,u) / ||T(I,u,..,u)|| (eq. T_Ivw,
+ * free mode 0), eigenvalues T(u,..,u) (eq. T_uvw), both with the median
+ * over the D sketches; the start with the largest eigenvalue gives
+ * lambda[k] and U[k][:]; then the sketch is deflated,
+ * FCS(T) <- FCS(T) - lambda_k FCS(u o .. o u) (linearity, eq. FCS_syn with
+ * R = 1).  fcsT is not modified (the deflation runs on a copy in the
+ * context's scratch).  init [K][L][I], lambda [K], U [K][I]: device.
+ * 2 <= N <= 8, 1 <= L <= 65535.
+ */
+int fcs_rtpm(fcs_ctx *ctx, int N, int64_t I, const int32_t *host_J, int D, const float *fcsT,
+             const int32_t *h, const int8_t *s, int64_t ldh, int K, int L, int n_iter,
+             const float *init, float *lambda, float *U);
+
+/*
+ * fcs_als -- sketched CP-ALS (ALS subsection) of rank R <= 32 for an
+ * order-N tensor from its sketches fcsT [D][Jt]: n_iter sweeps; for each
+ * mode m the columns [T(.., I (mode m), ..)]_r with the other factors' r-th
+ * columns (eq. T_Ivw, median over D), then F_m^T <- G^{-1} M^T with
+ * G = *_{n != m} F_n F_n^T (Cholesky) and column normalisation.
+ * host_F[n]: device [R][I_n], the transposed factor matrices (row r = column
+ * r of U_n): starting values in, unit-norm factors out; lambda [R] out.
+ */
+int fcs_als(fcs_ctx *ctx, int N, const int64_t *host_I, const int32_t *host_J, int D,
+            const float *fcsT, const int32_t *h, const int8_t *s, int64_t ldh, int R,
+            int n_iter, float *const *host_F, float *lambda);
 
 /*
  * fcs_recover -- entry estimates from sketches, the decompressing rule of the
@@ -371,6 +425,19 @@ int fcs_recover(fcs_ctx *ctx, int N, const int64_t *host_I,
  */
 int fcs_sketch_outer(fcs_ctx *ctx, int64_t nbatch, int D, int64_t La,
                      int64_t Lb, const float *fa, const float *fb, float *out);
+
+/*
+ * fcs_sketch_outer_sum -- sketch of a contraction over one mode from the
+ * sketches of its slices (tensor contraction compression): for A with
+ * slices A_l = A(:,:,l) and B with slices B_l = B(l,:,:),
+ *     FCS_d(A (x)_{3,1} B) = sum_l FCS_d(A_l) (*) FCS_d(B_l),
+ * the full linear convolutions summed in the frequency domain (one inverse
+ * per item and sketch).  fa [nbatch][L][D][La] (slice sketches with the
+ * hash tables of the first two modes), fb [nbatch][L][D][Lb] (the last
+ * two), out [nbatch][D][La+Lb-1].  L = 1 is fcs_sketch_outer.
+ */
+int fcs_sketch_outer_sum(fcs_ctx *ctx, int64_t nbatch, int64_t L, int D, int64_t La, int64_t Lb,
+                         const float *fa, const float *fb, float *out);
 
 #ifdef __cplusplus
 }

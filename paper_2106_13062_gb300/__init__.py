@@ -79,6 +79,17 @@ def lib() -> C.CDLL:
                                                     vp, vp, vp, C.c_int64, vp,
                                                     C.c_char_p, C.c_size_t]),
                 "fcs_cache_spectra": (C.c_int, [vp, C.c_int]),
+                "fcs_fold": (C.c_int, [vp, C.c_int64, C.c_int64, vp, C.c_int64, vp]),
+                "fcs_sketch_inner": (C.c_int, [vp, C.c_int, C.c_int64, C.c_int64, vp,
+                                               C.c_int64, vp, vp, vp, vp]),
+                "fcs_sketch_outer_sum": (C.c_int, [vp, C.c_int64, C.c_int64, C.c_int,
+                                                   C.c_int64, C.c_int64, vp, vp, vp]),
+                "fcs_rtpm": (C.c_int, [vp, C.c_int, C.c_int64, i32p, C.c_int, vp, vp,
+                                       vp, C.c_int64, C.c_int, C.c_int, C.c_int, vp,
+                                       vp, vp]),
+                "fcs_als": (C.c_int, [vp, C.c_int, i64p, i32p, C.c_int, vp, vp, vp,
+                                      C.c_int64, C.c_int, C.c_int,
+                                      C.POINTER(C.c_void_p), vp]),
                 "fcs_forget": (C.c_int, [vp, vp]),
                 "fcs_contract": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, i64p,
                                            i32p, C.c_int, vp, C.c_int64,
@@ -173,7 +184,8 @@ def exported_symbols():
             "fcs_last_error", "fcs_workspace_bytes", "fcs_make_hashes",
             "fcs_sketch_dense", "fcs_sketch_cp", "fcs_sketch_cp_noalloc",
             "fcs_contract", "fcs_cache_spectra", "fcs_forget",
-            "fcs_recover", "fcs_sketch_outer",
+            "fcs_fold", "fcs_sketch_inner", "fcs_rtpm", "fcs_als",
+            "fcs_recover", "fcs_sketch_outer", "fcs_sketch_outer_sum",
             "fcs_batch_plan_create", "fcs_batch_plan_launch",
             "fcs_batch_plan_destroy", "fcs_batch_sketch_cp", "fcs_batch_autotune",
             "fcs_server_create", "fcs_server_destroy", "fcs_server_submit",
@@ -474,6 +486,93 @@ def fcs_sketch_outer(ctx: Context, fa: torch.Tensor, fb: torch.Tensor):
     ctx.check(lib().fcs_sketch_outer(ctx.handle, nb, D, La, Lb, _ptr(fa),
                                      _ptr(fb), _ptr(out)))
     return out
+
+
+def fcs_sketch_outer_sum(ctx: Context, fa: torch.Tensor, fb: torch.Tensor):
+    """Tensor contraction compression: sum over slices l of the convolved
+    slice sketches.  fa [.., L, D, La], fb [.., L, D, Lb] -> [.., D, La+Lb-1]."""
+    ctx._sync_stream()
+    _need(fa, torch.float32, "fa")
+    _need(fb, torch.float32, "fb")
+    if fa.dim() < 3 or fa.shape[:-1] != fb.shape[:-1]:
+        raise ValueError("fa and fb must be [.., L, D, len] with equal leading dims")
+    Ls, D = fa.shape[-3], fa.shape[-2]
+    La, Lb = fa.shape[-1], fb.shape[-1]
+    nb = fa.numel() // (Ls * D * La)
+    out = torch.empty(fa.shape[:-3] + (D, La + Lb - 1), dtype=torch.float32,
+                      device=fa.device)
+    ctx.check(lib().fcs_sketch_outer_sum(ctx.handle, nb, Ls, D, La, Lb, _ptr(fa),
+                                         _ptr(fb), _ptr(out)))
+    return out
+
+
+def fcs_fold(ctx: Context, x: torch.Tensor, J: int):
+    """Tensor Sketch (Def. 2) from FCS sketches with every J_n = J: sum of the
+    bins congruent mod J.  x [.., Jt] -> [.., J]."""
+    ctx._sync_stream()
+    _need(x, torch.float32, "x")
+    Jt = x.shape[-1]
+    rows = x.numel() // Jt
+    out = torch.empty(x.shape[:-1] + (int(J),), dtype=torch.float32, device=x.device)
+    ctx.check(lib().fcs_fold(ctx.handle, rows, Jt, _ptr(x), int(J), _ptr(out)))
+    return out
+
+
+def fcs_sketch_inner(ctx: Context, sa: torch.Tensor, sw: torch.Tensor,
+                     bias: torch.Tensor | None = None, raw: bool = False):
+    """Compressed TRL (eq. net_compress): Y[b][c] = median_d <sa[b][d], sw[c][d]>
+    + bias[c].  sa [B, D, Jt], sw [C, D, Jt].  Returns Y [B, C] (and raw
+    [B, C, D] with raw=True)."""
+    ctx._sync_stream()
+    _need(sa, torch.float32, "sa")
+    _need(sw, torch.float32, "sw")
+    if bias is not None:
+        _need(bias, torch.float32, "bias")
+    Bn, D, Jt = sa.shape
+    Cn = sw.shape[0]
+    if sw.shape[1:] != (D, Jt):
+        raise ValueError("sw must be [C, D, Jt] like sa")
+    out = torch.empty((Bn, Cn), dtype=torch.float32, device=sa.device)
+    r = torch.empty((Bn, Cn, D), dtype=torch.float32, device=sa.device) if raw else None
+    ctx.check(lib().fcs_sketch_inner(ctx.handle, D, Jt, Bn, _ptr(sa), Cn, _ptr(sw),
+                                     _ptr(bias), _ptr(out), _ptr(r)))
+    return (out, r) if raw else out
+
+
+def fcs_rtpm(ctx: Context, fcsT: torch.Tensor, I: int, J, h, s, init: torch.Tensor,
+             n_iter: int, ldh: int = 0):
+    """Sketched robust tensor power method (symmetric order len(J)).  init
+    [K, L, I] starting vectors.  Returns (lambda [K], U [K, I])."""
+    ctx._sync_stream()
+    _need(fcsT, torch.float32, "fcsT")
+    _need(init, torch.float32, "init")
+    ldh = _tables(h, s, ldh)
+    K, L, Ii = init.shape
+    if Ii != int(I):
+        raise ValueError("init must be [K, L, I]")
+    lam = torch.empty(K, dtype=torch.float32, device=fcsT.device)
+    U = torch.empty((K, Ii), dtype=torch.float32, device=fcsT.device)
+    ctx.check(lib().fcs_rtpm(ctx.handle, len(J), int(I), _arr(C.c_int32, J), fcsT.shape[0],
+                             _ptr(fcsT), _ptr(h), _ptr(s), ldh, K, L, int(n_iter),
+                             _ptr(init), _ptr(lam), _ptr(U)))
+    return lam, U
+
+
+def fcs_als(ctx: Context, fcsT: torch.Tensor, I, J, h, s, F, n_iter: int, ldh: int = 0):
+    """Sketched CP-ALS.  F: list of N tensors [R, I_n] (transposed factors),
+    starting values in, unit-norm factors out (in place).  Returns lambda [R]."""
+    ctx._sync_stream()
+    _need(fcsT, torch.float32, "fcsT")
+    ldh = _tables(h, s, ldh)
+    for n, f in enumerate(F):
+        _need(f, torch.float32, f"F[{n}]")
+    R = F[0].shape[0]
+    lam = torch.empty(R, dtype=torch.float32, device=fcsT.device)
+    fp = (C.c_void_p * len(F))(*[f.data_ptr() for f in F])
+    ctx.check(lib().fcs_als(ctx.handle, len(I), _arr(C.c_int64, I), _arr(C.c_int32, J),
+                            fcsT.shape[0], _ptr(fcsT), _ptr(h), _ptr(s), ldh, R, int(n_iter),
+                            fp, _ptr(lam)))
+    return lam
 
 
 # ------------------------------------------------------------------ batching

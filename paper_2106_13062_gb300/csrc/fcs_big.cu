@@ -448,23 +448,38 @@ __global__ void free_gather_kernel(const float2 *__restrict__ Z, int64_t first_i
 }
 
 // ---------------------------------------------------------------- outer combine
-// zout[t] = packed conj of X_a * X_b for pairs j of transform t.
-__global__ void outer_combine_kernel(const float2 *__restrict__ Za, const float2 *__restrict__ Zb,
-                                     int64_t M, float2 *__restrict__ zout, int lp,
-                                     const float2 *__restrict__ tw) {
+// S[d][k] (+)= sum over the nl slices of the chunk of X_a[k] X_b[k] for the
+// pairs j of sketch d; Za/Zb hold transforms [l][d] of the chunk.  S is the
+// half spectrum [D][M+1] (bins 0 and M as reals in .x).
+__global__ void outer_accum_kernel(const float2 *__restrict__ Za, const float2 *__restrict__ Zb,
+                                   int64_t nl, int D, int64_t M, float2 *__restrict__ S,
+                                   int accumulate, int lp, const float2 *__restrict__ tw) {
   __shared__ float2 fine[kMaxFine];
   fill_fine(fine, lp);
   __syncthreads();
   const BigTw W{tw, fine, lp};
-  const int64_t t = blockIdx.y;
+  const int d = blockIdx.y;
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j > M / 2) return;
   const bool packed = j == 0;
-  float2 aa, ab, ba, bb;
-  half_pair(Za + t * M, M, j, W, aa, ab);
-  half_pair(Zb + t * M, M, j, W, ba, bb);
-  const float2 pa = pmul(aa, ba, packed), pb = pmul(ab, bb, false);
-  store_packed_pair(zout + t * M, M, j, pa, pb, W);
+  float2 sa = make_float2(0.f, 0.f), sb = sa;
+  for (int64_t l = 0; l < nl; ++l) {
+    const int64_t t = l * D + d;
+    float2 aa, ab, ba, bb;
+    half_pair(Za + t * M, M, j, W, aa, ab);
+    half_pair(Zb + t * M, M, j, W, ba, bb);
+    sa = cadd(sa, pmul(aa, ba, packed));
+    sb = cadd(sb, pmul(ab, bb, false));
+  }
+  float2 *Sd = S + int64_t(d) * (M + 1);
+  if (packed) {
+    const float x0 = accumulate ? Sd[0].x : 0.f, xm = accumulate ? Sd[M].x : 0.f;
+    Sd[0] = make_float2(x0 + sa.x, 0.f);
+    Sd[M] = make_float2(xm + sa.y, 0.f);
+  } else {
+    Sd[j] = accumulate ? cadd(Sd[j], sa) : sa;
+    if (2 * j != M) Sd[M - j] = accumulate ? cadd(Sd[M - j], sb) : sb;
+  }
 }
 
 unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) / per); }
@@ -675,48 +690,63 @@ int big_contract(fcs_ctx *ctx, const Modes &m, int kind, int free_mode, int D,
   return FCS_OK;
 }
 
-int big_outer(fcs_ctx *ctx, int64_t nbatch, int D, int64_t La, int64_t Lb, const float *fa,
-              const float *fb, float *out, int log2p) {
+int big_outer(fcs_ctx *ctx, int64_t nbatch, int64_t L, int D, int64_t La, int64_t Lb,
+              const float *fa, const float *fb, float *out, int log2p) {
   const int L1 = log2p - 1 - kL2;
   const int64_t M = int64_t(1) << (log2p - 1), P = 2 * M;
-  const int64_t total = nbatch * D;
-  const size_t per_t = sizeof(float) * size_t(P) * 3;          // Za, Zb, packed product
+  const size_t sbytes = (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
+  const size_t per_t = sizeof(float) * size_t(P);               // one transform
   const size_t cap = std::min(ctx->budget, kBigWorkspaceCap);
-  int64_t tc = std::max<int64_t>(1, int64_t(cap / per_t));
-  tc = std::min(tc, total);
+  // slices per chunk: Za and Zb hold nl * D transforms each; the packed
+  // inverse input (D transforms) reuses Za
+  int64_t nl = cap > sbytes ? int64_t((cap - sbytes) / (2 * per_t * D)) : 0;
+  nl = std::min(std::max<int64_t>(nl, 1), L);
+  const int64_t nbuf = nl * D;
   void *ws = nullptr;
-  int rc = ensure_workspace(ctx, per_t * size_t(tc), &ws);
+  int rc = ensure_workspace(ctx, sbytes + 2 * per_t * size_t(nbuf), &ws);
   if (rc) return rc;
-  float2 *Za = static_cast<float2 *>(ws);
-  float2 *Zb = Za + size_t(tc) * M;
-  float2 *zp = Zb + size_t(tc) * M;
+  float2 *S = static_cast<float2 *>(ws);
+  float2 *Za = reinterpret_cast<float2 *>(static_cast<char *>(ws) + sbytes);
+  float2 *Zb = Za + size_t(nbuf) * M;
   const int64_t Lo = La + Lb - 1;
-  for (int64_t g0 = 0; g0 < total; g0 += tc) {
-    const int64_t nt = std::min(tc, total - g0);
-    Pass1Args p{};
-    p.nlens = 1;
-    p.L1 = L1;
-    p.src = fa + g0 * La;
-    p.src_ld = La;
-    p.lens[0] = La;
-    rc = big_fft(ctx, p, nt, Za);
+  for (int64_t b = 0; b < nbatch; ++b) {
+    for (int64_t l0 = 0; l0 < L; l0 += nl) {
+      const int64_t cl = std::min(nl, L - l0);
+      const int64_t first = (b * L + l0) * D;                  // slice-sketch index
+      Pass1Args p{};
+      p.nlens = 1;
+      p.L1 = L1;
+      p.src = fa + first * La;
+      p.src_ld = La;
+      p.lens[0] = La;
+      rc = big_fft(ctx, p, cl * D, Za);
+      if (rc) return rc;
+      p.src = fb + first * Lb;
+      p.src_ld = Lb;
+      p.lens[0] = Lb;
+      rc = big_fft(ctx, p, cl * D, Zb);
+      if (rc) return rc;
+      outer_accum_kernel<<<dim3(blocks_for(M / 2 + 1, 256), unsigned(D)), 256, 0,
+                           ctx->stream>>>(Za, Zb, cl, D, M, S, l0 > 0 ? 1 : 0, log2p,
+                                          ctx->twiddle);
+      rc = check_cuda(ctx, cudaGetLastError(), "outer_accum_kernel");
+      if (rc) return rc;
+    }
+    float2 *zp = Za;
+    pack_inverse_kernel<<<dim3(blocks_for(M / 2, 256), unsigned(D)), 256, 0, ctx->stream>>>(
+        S, M + 1, M, zp, log2p, ctx->twiddle);
+    rc = check_cuda(ctx, cudaGetLastError(), "pack_inverse_kernel");
     if (rc) return rc;
-    p.src = fb + g0 * Lb;
-    p.src_ld = Lb;
-    p.lens[0] = Lb;
-    rc = big_fft(ctx, p, nt, Zb);
+    Pass1Args pi{};
+    pi.src = reinterpret_cast<const float *>(zp);
+    pi.src_ld = P;
+    pi.nlens = 1;
+    pi.lens[0] = P;
+    pi.L1 = L1;
+    rc = big_fft(ctx, pi, D, Zb);
     if (rc) return rc;
-    outer_combine_kernel<<<dim3(blocks_for(M / 2 + 1, 256), unsigned(nt)), 256, 0, ctx->stream>>>(
-        Za, Zb, M, zp, log2p, ctx->twiddle);
-    rc = check_cuda(ctx, cudaGetLastError(), "outer_combine_kernel");
-    if (rc) return rc;
-    p.src = reinterpret_cast<const float *>(zp);
-    p.src_ld = P;
-    p.lens[0] = P;
-    rc = big_fft(ctx, p, nt, Za);
-    if (rc) return rc;
-    unpack_real_kernel<<<dim3(blocks_for(Lo, 256), unsigned(nt)), 256, 0, ctx->stream>>>(
-        Za, M, 1.0f / float(M), out + g0 * Lo, Lo, Lo);
+    unpack_real_kernel<<<dim3(blocks_for(Lo, 256), unsigned(D)), 256, 0, ctx->stream>>>(
+        Zb, M, 1.0f / float(M), out + b * D * Lo, Lo, Lo);
     rc = check_cuda(ctx, cudaGetLastError(), "unpack_real_kernel");
     if (rc) return rc;
   }

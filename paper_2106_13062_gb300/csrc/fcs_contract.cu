@@ -35,6 +35,7 @@ struct fcs_spec_cache {
     cudaEvent_t ready;   // spectrum written
     cudaEvent_t used;    // last contraction that read it
     uint64_t tick;
+    bool stale;          // key's contents may have changed: recompute on next use
   };
   std::vector<Entry> e;
   size_t bytes = 0;
@@ -73,6 +74,15 @@ fcs_spec_cache::Entry *spec_cache_get(fcs_ctx *ctx, const float *key, int64_t Jt
   for (auto &x : c->e) {
     if (x.key == key && x.Jt == Jt && x.D == D && x.log2m == log2m) {
       x.tick = c->tick;
+      if (x.stale) {
+        // recompute into the same memory once its last readers are done
+        if (cudaStreamWaitEvent(ctx->stream, x.used, 0) != cudaSuccess) {
+          cudaGetLastError();
+          return nullptr;
+        }
+        x.stale = false;
+        return &x;
+      }
       *hit = true;
       return &x;
     }
@@ -86,7 +96,7 @@ fcs_spec_cache::Entry *spec_cache_get(fcs_ctx *ctx, const float *key, int64_t Jt
       if (c->e[i].tick < c->e[lru].tick) lru = i;
     spec_cache_erase(c, lru);
   }
-  fcs_spec_cache::Entry x{key, Jt, D, log2m, nullptr, bytes, nullptr, nullptr, c->tick};
+  fcs_spec_cache::Entry x{key, Jt, D, log2m, nullptr, bytes, nullptr, nullptr, c->tick, false};
   if (cudaMalloc(&x.spec, bytes) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
@@ -338,9 +348,9 @@ void spec_cache_invalidate(fcs_ctx *ctx, const void *p, size_t bytes) {
   fcs_spec_cache *c = ctx ? ctx->spec_cache : nullptr;
   if (!c) return;
   const char *lo = static_cast<const char *>(p);
-  for (size_t i = c->e.size(); i-- > 0;) {
-    const char *k = reinterpret_cast<const char *>(c->e[i].key);
-    if (k >= lo && k < lo + bytes) spec_cache_erase(c, i);
+  for (auto &x : c->e) {
+    const char *k = reinterpret_cast<const char *>(x.key);
+    if (k >= lo && k < lo + bytes) x.stale = true;
   }
 }
 
@@ -370,9 +380,8 @@ extern "C" int fcs_forget(fcs_ctx *ctx, const void *ptr) {
   ctx->err.clear();
   fcs_spec_cache *c = ctx->spec_cache;
   if (!c || !ptr) return FCS_OK;
-  DeviceGuard g(ctx->device);
-  for (size_t i = c->e.size(); i-- > 0;)
-    if (c->e[i].key == ptr) spec_cache_erase(c, i);
+  for (auto &x : c->e)
+    if (x.key == ptr) x.stale = true;        // recomputed on next use; no host wait
   return FCS_OK;
 }
 
@@ -458,7 +467,7 @@ extern "C" int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
                                                       ent ? ent->ready : nullptr));
   }
   if (rc) {
-    if (ent && !hit) fcs_forget(ctx, fcsT);      // never computed
+    if (ent && !hit) ent->stale = true;          // never computed
     return rc;
   }
   if (ent) {

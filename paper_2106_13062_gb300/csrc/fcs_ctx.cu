@@ -169,6 +169,7 @@ extern "C" int fcs_destroy(fcs_ctx *ctx) {
   spec_cache_destroy(ctx);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->raw) cudaFree(ctx->raw);
+  if (ctx->algo) cudaFree(ctx->algo);
   if (ctx->twiddle) cudaFree(ctx->twiddle);
   delete ctx;
   return FCS_OK;

@@ -36,6 +36,8 @@ struct fcs_ctx {
   bool cache_spectra = false;                    // fcs_cache_spectra
   float *raw = nullptr;          // per-sketch estimates of long contractions
   size_t raw_bytes = 0;
+  void *algo = nullptr;          // scratch of fcs_rtpm / fcs_als
+  size_t algo_bytes = 0;
   std::string err;
 };
 
@@ -481,7 +483,7 @@ int big_contract(fcs_ctx *ctx, const Modes &m, int kind, int free_mode, int D,
                  const float *fcsT, int64_t B, const float *const *vec, const int32_t *h,
                  const int8_t *s, float2 *spec, bool need_spec, cudaEvent_t spec_ready,
                  float *raw, int log2p);
-int big_outer(fcs_ctx *ctx, int64_t nbatch, int D, int64_t La, int64_t Lb, const float *fa,
-              const float *fb, float *out, int log2p);
+int big_outer(fcs_ctx *ctx, int64_t nbatch, int64_t L, int D, int64_t La, int64_t Lb,
+              const float *fa, const float *fb, float *out, int log2p);
 
 }  // namespace fcs
