@@ -174,7 +174,7 @@ class CpWorkload:
         return self.D
 
     def launches_per_step(self):
-        return 3                     # hashes, one factor transpose, cp_kernel
+        return 3                     # hashes, prep (transpose + clear), sketch kernel
 
     def flops(self):
         """2.5 P log2 P per real FFT of length P (D*R*N forward + D inverse)

@@ -3,9 +3,9 @@
 // with P the smallest power of two >= Jt (any P >= Jt gives the exact linear
 // convolution, so out = the first Jt samples).
 //
-// Two kernels.  (1) A transpose writes the factor columns contiguously
-// (lambda folded into mode 1) so every column load is coalesced.  (2) The
-// fused sketch kernel: CTA (g, d) owns sketch d and a contiguous group of
+// Two kernels.  (1) prep_kernel writes the factor columns contiguously
+// (lambda folded into mode 1) so every column load is coalesced, and clears
+// the spectrum accumulator.  (2) The fused sketch kernel: CTA (g, d) owns sketch d and a contiguous group of
 // ranks.  For each rank and mode it scatters the signed factor column into a
 // compact shared-memory buffer of max_n J_n reals (the Count Sketch of
 // Def. 1; the zero padding up to P is never stored), runs the block real FFT
@@ -20,6 +20,7 @@
 // into registers while the current column is transformed.  For P = 16384
 // the kernel runs on the warp-DIT engine instead (cp13_kernel): two block
 // barriers per transform, the next column scattered between them.
+#include <algorithm>
 #include <cstdarg>
 #include <mutex>
 
@@ -51,30 +52,6 @@ struct TransposeArgs {
   const float *lambda;
   float *UT;
 };
-
-// UT[n][r][i] = U_n[i*ld + r] (times lambda_r for n = 0).
-__global__ void transpose_all_kernel(TransposeArgs t) {
-  __shared__ float tile[32][33];
-  const int n = blockIdx.z;
-  const int64_t I = t.I[n], R = t.R, ld = t.ld[n];
-  const float *U = t.U[n];
-  const float *lambda = n == 0 ? t.lambda : nullptr;
-  float *UT = t.UT + t.ut_off[n];
-  const int64_t i0 = blockIdx.x * 32ll, r0 = blockIdx.y * 32ll;
-  if (i0 >= I) return;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int64_t i = i0 + k, r = r0 + threadIdx.x;
-    if (i < I && r < R) tile[k][threadIdx.x] = U[i * ld + r];
-  }
-  __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int64_t r = r0 + k, i = i0 + threadIdx.x;
-    if (i < I && r < R) {
-      const float lam = lambda ? __ldg(lambda + r) : 1.f;
-      UT[r * I + i] = tile[threadIdx.x][k] * lam;
-    }
-  }
-}
 
 // Shared-memory layout of cp_kernel; every region starts on a 16-byte
 // boundary (the scatter buffer is cleared with float4 stores).
@@ -443,6 +420,52 @@ __global__ void __launch_bounds__(wdit::kNT) cp13_kernel(CpArgs a, const float2 
   if (tid == 0) a.counter[d] = 0u;
 }
 
+// prep_kernel: in one launch, the factor transpose in 32 x 32 tiles,
+// UT[n][r][i] = U_n[i*ld + r] (times lambda_r for n = 0), and the clearing
+// of the spectrum accumulator and tickets.  256 threads per block.
+struct PrepArgs {
+  TransposeArgs t;
+  int64_t tiles_x, tiles_y, ntile;     // transpose tiles per mode and in total
+  float4 *zero;
+  int64_t zero_n4;
+  int zero_blocks;
+};
+
+__global__ void __launch_bounds__(256) prep_kernel(PrepArgs a) {
+  const int64_t b = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (b < a.ntile) {
+    __shared__ float tile[32][33];
+    const int64_t per = a.tiles_x * a.tiles_y;
+    const int n = int(b / per);
+    const int64_t rem = b % per;
+    const int64_t bx = rem % a.tiles_x, by = rem / a.tiles_x;
+    const int64_t I = a.t.I[n], R = a.t.R, ld = a.t.ld[n];
+    const float *U = a.t.U[n];
+    const float *lambda = n == 0 ? a.t.lambda : nullptr;
+    float *UT = a.t.UT + a.t.ut_off[n];
+    const int64_t i0 = bx * 32, rr0 = by * 32;
+    if (i0 >= I) return;
+    const int tx = tid & 31, ty = tid >> 5;
+    for (int k = ty; k < 32; k += 8) {
+      const int64_t i = i0 + k, r = rr0 + tx;
+      if (i < I && r < R) tile[k][tx] = U[i * ld + r];
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+      const int64_t r = rr0 + k, i = i0 + tx;
+      if (i < I && r < R) {
+        const float lam = lambda ? __ldg(lambda + r) : 1.f;
+        UT[r * I + i] = tile[tx][k] * lam;
+      }
+    }
+    return;
+  }
+  const int64_t zb = b - a.ntile;
+  for (int64_t e = zb * 256 + tid; e < a.zero_n4; e += int64_t(a.zero_blocks) * 256)
+    a.zero[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // Kernel for the given prefetch depth and scatter-buffer height.
 template <int CPT>
 const void *cp13_pick_rmax(int ra) {
@@ -560,25 +583,29 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
   a.UT = UT;
   DeviceGuard g(ctx->device);
   spec_cache_invalidate(ctx, out, sizeof(float) * size_t(D) * size_t(a.m.Jt));
-  rc = check_cuda(ctx, cudaMemsetAsync(ws, 0, gbytes + cbytes, ctx->stream),
-                  "cudaMemsetAsync(cp workspace)");
-  if (rc) return rc;
   {
-    TransposeArgs t{};
+    // one launch: factor transpose (lambda folded into mode 1) and clearing
+    // of the accumulator and tickets
+    PrepArgs pa{};
     for (int n = 0; n < N; ++n) {
-      t.U[n] = host_U[n];
-      t.I[n] = host_I[n];
-      t.ld[n] = host_ldU[n];
-      t.ut_off[n] = a.ut_off[n];
+      pa.t.U[n] = host_U[n];
+      pa.t.I[n] = host_I[n];
+      pa.t.ld[n] = host_ldU[n];
+      pa.t.ut_off[n] = a.ut_off[n];
     }
-    t.R = R;
-    t.lambda = lambda;
-    t.UT = UT;
-    dim3 grid(unsigned((Imax + 31) / 32), unsigned((R + 31) / 32), unsigned(N));
-    if (grid.y > 65535 || grid.x > 0x7fffffffu)
-      return set_error(ctx, FCS_EUNSUPPORTED, "factor matrices too large");
-    transpose_all_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(t);
-    rc = check_cuda(ctx, cudaGetLastError(), "transpose_all_kernel");
+    pa.t.R = R;
+    pa.t.lambda = lambda;
+    pa.t.UT = UT;
+    pa.tiles_x = (Imax + 31) / 32;
+    pa.tiles_y = (R + 31) / 32;
+    pa.ntile = pa.tiles_x * pa.tiles_y * N;
+    pa.zero = static_cast<float4 *>(ws);
+    pa.zero_n4 = int64_t(gbytes + cbytes) / 16;
+    pa.zero_blocks = int(std::min<int64_t>(64, (pa.zero_n4 + 255) / 256));
+    const int64_t blocks = pa.ntile + pa.zero_blocks;
+    if (blocks > 0x7fffffffLL) return set_error(ctx, FCS_EUNSUPPORTED, "factor matrices too large");
+    prep_kernel<<<unsigned(blocks), 256, 0, ctx->stream>>>(pa);
+    rc = check_cuda(ctx, cudaGetLastError(), "prep_kernel");
     if (rc) return rc;
   }
   rc = FCS_EUNSUPPORTED;
@@ -777,28 +804,29 @@ extern "C" int fcs_sketch_cp_noalloc(void *stream, int N, const int64_t *host_I,
   a.counter = reinterpret_cast<unsigned *>(sd->scratch + gbytes);
   float *UT = reinterpret_cast<float *>(sd->scratch + gbytes + cbytes);
   a.UT = UT;
-  // the accumulator and tickets must start at zero; the array keeps the
-  // previous call's contents otherwise
-  e = cudaMemsetAsync(sd->scratch, 0, gbytes + cbytes, st);
-  if (e != cudaSuccess)
-    return noalloc_fail(err, err_len, FCS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  // the accumulator and tickets must start at zero (the array keeps the
+  // previous call's contents); the same launch transposes the factors
   {
-    TransposeArgs t{};
+    PrepArgs pa{};
     for (int n = 0; n < N; ++n) {
-      t.U[n] = host_U[n];
-      t.I[n] = host_I[n];
-      t.ld[n] = host_ldU[n];
-      t.ut_off[n] = a.ut_off[n];
+      pa.t.U[n] = host_U[n];
+      pa.t.I[n] = host_I[n];
+      pa.t.ld[n] = host_ldU[n];
+      pa.t.ut_off[n] = a.ut_off[n];
     }
-    t.R = R;
-    t.lambda = lambda;
-    t.UT = UT;
-    dim3 grid(unsigned((Imax + 31) / 32), unsigned((R + 31) / 32), unsigned(N));
-    if (grid.y > 65535) return noalloc_fail(err, err_len, FCS_EUNSUPPORTED, "rank too large");
-    transpose_all_kernel<<<grid, dim3(32, 8), 0, st>>>(t);
+    pa.t.R = R;
+    pa.t.lambda = lambda;
+    pa.t.UT = UT;
+    pa.tiles_x = (Imax + 31) / 32;
+    pa.tiles_y = (R + 31) / 32;
+    pa.ntile = pa.tiles_x * pa.tiles_y * N;
+    pa.zero = reinterpret_cast<float4 *>(sd->scratch);
+    pa.zero_n4 = int64_t(gbytes + cbytes) / 16;
+    pa.zero_blocks = int(std::min<int64_t>(64, (pa.zero_n4 + 255) / 256));
+    prep_kernel<<<unsigned(pa.ntile + pa.zero_blocks), 256, 0, st>>>(pa);
     e = cudaGetLastError();
     if (e != cudaSuccess)
-      return noalloc_fail(err, err_len, FCS_ECUDA, "transpose: %s", cudaGetErrorString(e));
+      return noalloc_fail(err, err_len, FCS_ECUDA, "prep: %s", cudaGetErrorString(e));
   }
   rc = FCS_EUNSUPPORTED;
   FCS_DISPATCH_LOG2M(log2m, rc = noalloc_launch_cp<L>(a, groups, Imax, sd->twiddle, st, err,

@@ -527,12 +527,14 @@ __device__ __forceinline__ void step1(float2 *A2, int ra, float2 *B, const float
 }
 
 // Step 2 up to the complex spectrum: v[q1] = Z[q2 + 512 q1], q2 = q2_of(threadIdx.x).
+// RS: row stride of B (float2).
+template <int RS = kRS>
 __device__ __forceinline__ void step2_complex(const float2 *B, const float2 *tws,
                                               float2 (&v)[16]) {
   const int t = threadIdx.x;
   const int q2 = q2_of(t);
 #pragma unroll
-  for (int w = 0; w < 16; ++w) v[w] = B[w * kRS + q2];
+  for (int w = 0; w < 16; ++w) v[w] = B[w * RS + q2];
   {
     float2 wp[4];                                   // W_M^(q2 2^b)
 #pragma unroll
@@ -558,10 +560,11 @@ __device__ __forceinline__ void unpack2_twice(float2 za, float2 zb, float2 w, fl
 // of the unpack; callers divide it out at the end); for thread 0, v[0] packs
 // the two real bins (2 X[0], 2 X[M]).  `stash` is 16 float2 of shared scratch
 // used by thread 0.  Every lane of every warp must call it (it shuffles).
+template <int RS = kRS>
 __device__ __forceinline__ void step2(const float2 *B, const float2 *tws, float2 *stash,
                                       float2 (&v)[16]) {
   const int t = threadIdx.x;
-  step2_complex(B, tws, v);                         // v[q1] = Z[q2 + 512 q1]
+  step2_complex<RS>(B, tws, v);                     // v[q1] = Z[q2 + 512 q1]
   if (t == 0) {
 #pragma unroll
     for (int q1 = 0; q1 < 16; ++q1) stash[q1] = v[q1];
