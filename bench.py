@@ -237,7 +237,7 @@ class CpWorkload:
         peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
         ach = self.flops() / (t / 1e3) / 1e12
         files = ["fcs_cp.cu", "fcs_fft.cuh", "fcs_internal.cuh"]
-        return {"kernel": "cp_kernel (fcs_sketch_cp: factor transpose + fused sketch)",
+        return {"kernel": "cp13_kernel (fcs_sketch_cp: prep launch + fused sketch)",
                 "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak,
                 "traffic": profiled_traffic("cp_kernel_order3_I1000_R100_J5000_D10.txt", files),
@@ -649,7 +649,9 @@ class BatchWorkload:
         ach = flops / (t / 1e3) / 1e12
         return {"kernel": "batch (transpose + persistent batch_cp_kernel, graph replay)",
                 "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
+                "frac": ach / peak,
+                "traffic": profiled_traffic("batch_cp_kernel_mixed64.txt",
+                                            ["fcs_batch.cu", "fcs_fft.cuh", "fcs_internal.cuh"]),
                 "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes "
                                f"x 2 flop/FMA x {sm_mhz:.0f} MHz",
                 "avg_launch_ms": t, "grain": self.grain,
