@@ -898,6 +898,25 @@ def run_reference(args, rank, world):
     }
 
 
+def reduce_max_over_ranks(values, world):
+    """Per-rank timings -> their maxima over all ranks (replicas: the slowest
+    rank sets the job's time).  Works with NCCL (device tensors) and gloo."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    dev = (torch.device("cuda", torch.cuda.current_device())
+           if dist.get_backend() == "nccl" else torch.device("cpu"))
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_rate(world, units_per_step, steps, time_ms):
+    """Whole-job throughput: units all ranks processed / the slowest rank's time."""
+    return world * units_per_step * steps / (time_ms / 1e3)
+
+
 def run_fcs(args, rank, world, local_rank):
     import torch
     import paper_2106_13062_gb300 as fcs
@@ -961,11 +980,7 @@ def run_fcs(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in ev) / e2e_steps
 
-    tmax = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms, e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tmax, e2e_ms = float(t[0]), float(t[1])
+    tmax, e2e_ms = reduce_max_over_ranks([total_ms, e2e_ms], world)
     props = torch.cuda.get_device_properties(local_rank)
     roof = w.roofline(times, props)
     ctx.close()
@@ -973,7 +988,7 @@ def run_fcs(args, rank, world, local_rank):
         return None
     per_step = w.sketches_per_step()
     res = {
-        "impl": "fcs", "metric": w.metric, "value": world * per_step * args.steps / (tmax / 1e3),
+        "impl": "fcs", "metric": w.metric, "value": job_rate(world, per_step, args.steps, tmax),
         "unit": "sketches/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -981,7 +996,7 @@ def run_fcs(args, rank, world, local_rank):
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                        l2="flushed between timed steps (256 MiB write)"),
         "roofline": roof,
-        "e2e": {"value": world * per_step / (e2e_ms / 1e3), "unit": "sketches/s",
+        "e2e": {"value": job_rate(world, per_step, 1, e2e_ms), "unit": "sketches/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms},
         "gpu_launches": w.launches_per_step() * args.steps,

@@ -170,6 +170,7 @@ def test_cp_tiny_and_dense_agree(fcs, ctx, orc):
     ([40, 700, 30, 1200], [4000, 3000, 2000, 5000], 4, 2, {"ld_pad": 3}),
     ([50, 60, 70], [8192, 4096, 2048], 2, 16, {}),
     ([100], [16384], 2, 1, {}),
+    ([200, 150, 100, 120], [4000, 4000, 4000, 4000], 3, 2, {}),   # 4-row scatter buffer
 ])
 def test_cp_shapes(fcs, ctx, orc, I, J, R, D, kw):
     _cp_case(fcs, ctx, orc, I, J, R, D, 21, **kw)
