@@ -236,7 +236,7 @@ class CpWorkload:
         sm_mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
         peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
         ach = self.flops() / (t / 1e3) / 1e12
-        files = ["fcs_cp.cu", "fcs_fft.cuh", "fcs_internal.cuh"]
+        files = ["fcs_cp.cu", "fcs_cp_run.cuh", "fcs_fft.cuh", "fcs_internal.cuh"]
         return {"kernel": "cp13_kernel (fcs_sketch_cp: prep launch + fused sketch)",
                 "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak,
@@ -544,11 +544,12 @@ def long_cp_launches(J) -> int:
 
 
 class BatchWorkload:
-    """64 heterogeneous CP problems per step in one persistent launch (CUDA
-    graph replay of a prepared plan); the plain path runs one fcs_sketch_cp
-    per problem.  Unit: sketches/s."""
+    """64 heterogeneous CP problems per step in one batched launch chain (a
+    transpose, then one kernel per FFT size; CUDA graph replay of a prepared
+    plan); the plain path runs one fcs_sketch_cp per problem.  Unit:
+    sketches/s."""
     name = "batch_cp_mixed64"
-    metric = "FCS sketches/s (64 mixed CP problems per step, batched persistent launch)"
+    metric = "FCS sketches/s (64 mixed CP problems per step, batched launch chain)"
     count, seed = 64, 5
 
     def __init__(self):
@@ -565,10 +566,11 @@ class BatchWorkload:
         return sum(D for _, _, _, D in self.shapes)
 
     def launches_per_step(self):
-        # batched transpose + persistent kernel; problems with P > 16384 run
-        # on the two-pass long-FFT route after it
-        return 2 + sum(long_cp_launches(J) for _, J, _, _ in self.shapes
-                       if fft_len(jt_of(J)) > 16384)
+        # batched transpose + one kernel per FFT size; problems with
+        # P > 16384 run on the two-pass long-FFT route after them
+        sizes = {fft_len(jt_of(J)) for _, J, _, _ in self.shapes if fft_len(jt_of(J)) <= 16384}
+        return 1 + len(sizes) + sum(long_cp_launches(J) for _, J, _, _ in self.shapes
+                                    if fft_len(jt_of(J)) > 16384)
 
     def setup(self, fcs, ctx, dev):
         import torch
@@ -597,7 +599,7 @@ class BatchWorkload:
         torch.cuda.synchronize()
 
     def step(self, k, marks):
-        marks("batch_cp_kernel")
+        marks("batch")
         self.graph.replay()
         marks(None)
 
@@ -626,7 +628,7 @@ class BatchWorkload:
 
     def roofline(self, times_ms, props):
         import torch
-        t = statistics.mean(times_ms["batch_cp_kernel"])
+        t = statistics.mean(times_ms["batch"])
         flops = 0.0
         for I, J, R, D in self.shapes:
             P = fft_len(jt_of(J))
@@ -647,11 +649,12 @@ class BatchWorkload:
         sm_mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
         peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
         ach = flops / (t / 1e3) / 1e12
-        return {"kernel": "batch (transpose + persistent batch_cp_kernel, graph replay)",
+        return {"kernel": "batch (transpose + batch_class_kernel per FFT size, graph replay)",
                 "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak,
-                "traffic": profiled_traffic("batch_cp_kernel_mixed64.txt",
-                                            ["fcs_batch.cu", "fcs_fft.cuh", "fcs_internal.cuh"]),
+                "traffic": profiled_traffic("batch_class_kernels_mixed64.txt",
+                                            ["fcs_batch.cu", "fcs_cp_run.cuh", "fcs_fft.cuh",
+                                             "fcs_internal.cuh"]),
                 "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes "
                                f"x 2 flop/FMA x {sm_mhz:.0f} MHz",
                 "avg_launch_ms": t, "grain": self.grain,
@@ -858,10 +861,10 @@ def run_serve(args, rank, world, local_rank):
             "saturation_p50_s": float(np.percentile(lat_sat, 50)),
             "saturation_p99_s": float(np.percentile(lat_sat, 99)),
         },
-        # saturation run: per round a batched transpose + persistent kernel,
-        # per CP request a hash kernel, per contraction spectrum + contract +
-        # median kernels
-        "gpu_launches": int(2 * st_sat.rounds + sum(1 for r in reqs if r[0] == "cp")
+        # saturation run: per round a batched transpose + one kernel per FFT
+        # size (counted by the server), per CP request a hash kernel, per
+        # contraction spectrum + contract + median kernels
+        "gpu_launches": int(st_sat.batch_launches + sum(1 for r in reqs if r[0] == "cp")
                             + 3 * sum(1 for r in reqs if r[0] == "ct")),
     }
     return res

@@ -281,6 +281,8 @@ typedef struct fcs_stats {
   size_t arena_used;
   double p50_latency_s, p99_latency_s, mean_latency_s;
   double busy_s;            /* first submit -> last completion */
+  int64_t batch_launches;   /* kernels of the rounds' batched CP launches
+                               (a transpose and one per FFT size, per round) */
 } fcs_stats;
 
 /* Start a server (allocates the arena, staging and streams once). */

@@ -175,7 +175,8 @@ class Stats(C.Structure):
                 ("rounds", C.c_int64), ("sketches", C.c_int64),
                 ("max_inflight_seen", C.c_int64), ("arena_used", C.c_size_t),
                 ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double),
-                ("mean_latency_s", C.c_double), ("busy_s", C.c_double)]
+                ("mean_latency_s", C.c_double), ("busy_s", C.c_double),
+                ("batch_launches", C.c_int64)]
 
 
 def exported_symbols():

@@ -1,21 +1,23 @@
 // fcs_batch.cu -- fcs_batch_sketch_cp / fcs_batch_autotune: many CP-route
-// sketches (eq. FCS_syn) of uneven order, sizes, rank and sketch length in one
-// persistent launch.
+// sketches (eq. FCS_syn) of uneven order, sizes, rank and sketch length in a
+// few launches.
 //
 // Host side (fcs_batch_plan_create): the work is cut into items (problem p,
-// sketch d, group of `grain` ranks), ordered largest-FFT first, and uploaded
-// once with the problem descriptors into plan-owned device memory.  A launch
+// sketch d, group of `grain` ranks), grouped by FFT size (largest first;
+// within a size, the longest items first), and uploaded once with the
+// problem descriptors into plan-owned device memory.  A launch
 // (fcs_batch_plan_launch) issues only device work -- clear the accumulators,
-// transpose every problem's factor columns in one batched launch, run the
-// persistent kernel -- so it can be captured into a CUDA graph and replayed.
-// Device side: a persistent kernel (one CTA per SM, 512 threads) pulls items
-// from an atomic counter.  Each item dispatches on its
-// problem's FFT length to the same block real FFT as fcs_sketch_cp (count
-// sketch into a compact shared buffer, Stockham passes, fused last pass and
-// unpack, mode product in registers, rank sum in shared memory), adds its
-// partial spectrum into the problem's accumulator, and the item that
-// completes sketch (p, d) (ticket counter) runs that sketch's inverse FFT.
-// The queue only counts up; no CTA ever waits on another.
+// transpose every problem's factor columns in one batched launch, run one
+// kernel per FFT size -- so it can be captured into a CUDA graph and
+// replayed.  Device side: each size class runs with the block size and
+// engine of the single-problem kernel for that size (cp_run / cp13_run of
+// fcs_cp_run.cuh), one CTA per item: count sketch into a compact shared
+// buffer, block real FFT, mode product in registers, rank sum in shared
+// memory, the item's partial spectrum into the problem's accumulator, and
+// the item that completes sketch (p, d) (ticket counter) runs that sketch's
+// inverse FFT.  The class launches form a chain of programmatic dependent
+// launches, so a class starts while the previous one drains.  No CTA ever
+// waits on another CTA of its own grid.
 //
 // The grain (ranks per item) trades load balance against the number of
 // partial-spectrum flushes.  fcs_batch_autotune times the whole batch for
@@ -32,7 +34,7 @@
 #include <vector>
 
 #include "fcs_batch_internal.cuh"
-#include "fcs_fft.cuh"
+#include "fcs_cp_run.cuh"
 
 struct fcs_batch_state {
   std::map<uint64_t, int> tuned;   // batch signature -> grain
@@ -54,8 +56,6 @@ struct fcs_batch_plan {
 
 namespace fcs {
 namespace {
-
-constexpr int kBatchNT = 512;
 
 struct BatchProb {
   int N, D, L, sb;
@@ -107,209 +107,123 @@ __global__ void batch_transpose_kernel(const TransposeTask *__restrict__ tasks, 
   }
 }
 
-template <int L>
-struct BatchSmem {
-  static constexpr size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
-  static constexpr size_t kB = 0;
-  static constexpr size_t kAcc = up16(sizeof(float2) * padded_len(1 << L));
-  static constexpr size_t kTw = up16(kAcc + sizeof(float2) * LastPass<L, kBatchNT>::NV * kBatchNT);
-  static constexpr size_t kA = up16(kTw + sizeof(float2) * plan_twlen(L));
-  static size_t bytes(int sb) { return kA + sizeof(float) * size_t(sb); }
+// cp_run / cp13_run's accessors over a problem descriptor (fcs_cp_run.cuh).
+struct BatchView {
+  const BatchProb &P;
+  int sb;
+  __device__ __forceinline__ int modes() const { return P.N; }
+  __device__ __forceinline__ int64_t dim(int n) const { return P.I[n]; }
+  __device__ __forceinline__ const float *column(int n, int64_t r) const {
+    return P.UT + P.ut_off[n] + r * P.I[n];
+  }
+  __device__ __forceinline__ const int32_t *hashes(int d, int n) const {
+    return P.h + d * P.ldh + P.off[n];
+  }
+  __device__ __forceinline__ const int8_t *signs(int d, int n) const {
+    return P.s + d * P.ldh + P.off[n];
+  }
+  __device__ __forceinline__ int64_t length() const { return P.Jt; }
+  __device__ __forceinline__ float *sketch(int d) const { return P.out + d * P.Jt; }
+  __device__ __forceinline__ float2 *spectrum() const { return P.G; }
+  __device__ __forceinline__ unsigned *ticket(int d) const { return P.tickets + d; }
 };
 
-// One work item: ranks [r0, r1) of sketch d of problem P.
+// Programmatic dependent launch.  launch_dependents lets the next launch of
+// the chain start once every CTA of this grid has issued it (so every CTA of
+// this grid is already resident: the next grid can never hold the SMs this
+// one still needs).  wait_previous returns once the previous grid of the
+// chain has completed and its writes are visible; called at a CTA's end, it
+// makes each grid complete after its predecessor, so work queued after the
+// chain waits for all of it.  Both are no-ops in a launch made without the
+// programmatic-serialisation attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait_previous() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// One CTA per item (problem, sketch d, rank group) of one FFT-size class,
+// P = 2^(LOG2M+1) <= 8192, NT = 2^(LOG2M-4) threads.
+template <int LOG2M, int NT, int CPT>
+__global__ void __launch_bounds__(NT) batch_class_kernel(const BatchProb *__restrict__ probs,
+                                                         const int4 *__restrict__ items,
+                                                         const float2 *__restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int is_last;
+  pdl_launch_dependents();
+  const int4 w = items[blockIdx.x];
+  const BatchProb &P = probs[w.x];
+  const int64_t r0 = int64_t(w.z) * P.rpi;
+  const int64_t r1 = min(P.R, r0 + P.rpi);
+  const BatchView view{P, P.sb};
+  cp_run<LOG2M, NT, CPT>(view, w.y, r0, r1, unsigned(P.groups), smem_raw, tw, &is_last);
+  pdl_wait_previous();
+}
+
+// The same for P = 16384 on the warp-DIT engine (ra <= 32 RMAX).
+template <int CPT, int RMAX>
+__global__ void __launch_bounds__(wdit::kNT) batch_class13_kernel(
+    const BatchProb *__restrict__ probs, const int4 *__restrict__ items,
+    const float2 *__restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int is_last;
+  pdl_launch_dependents();
+  const int4 w = items[blockIdx.x];
+  const BatchProb &P = probs[w.x];
+  const int64_t r0 = int64_t(w.z) * P.rpi;
+  const int64_t r1 = min(P.R, r0 + P.rpi);
+  const BatchView view{P, P.sb};
+  cp13_run<CPT, RMAX>(view, w.y, r0, r1, unsigned(P.groups), smem_raw, tw, &is_last);
+  pdl_wait_previous();
+}
+
+// Kernel, block size and shared memory of a class: FFT size L, prefetch
+// depth from the longest mode (entries per thread), scatter buffer sb.
+struct ClassKernel {
+  const void *fn;
+  int nt;
+  size_t smem;
+};
+
 template <int L>
-__device__ __noinline__ void batch_item(const BatchProb &P, int d, int64_t r0, int64_t r1,
-                           unsigned char *smem, const float2 *__restrict__ tw,
-                           bool fill_tw, int *s_flag) {
-  constexpr int NT = kBatchNT;
-  constexpr int CPT = 2;
-  using LPs = LastPass<L, NT>;
-  using Lay = BatchSmem<L>;
-  constexpr int M = 1 << L;
-  constexpr int HALF = M / 2;
-  constexpr int RL = LPs::RL, EPS = LPs::EPS, NV = LPs::NV;
-  float2 *B = reinterpret_cast<float2 *>(smem + Lay::kB);
-  float2 *accS = reinterpret_cast<float2 *>(smem + Lay::kAcc);
-  float2 *tws = reinterpret_cast<float2 *>(smem + Lay::kTw);
-  float *A = reinterpret_cast<float *>(smem + Lay::kA);
-  const int tid = threadIdx.x;
-  const int sb = P.sb;
-  const int N = P.N;
-
-  if (fill_tw) fill_twiddles<L, NT>(tws, tw);
-  for (int e = tid; e < sb / 4; e += NT)
-    reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) accS[v * NT + tid] = make_float2(0.f, 0.f);
-
-  float pv[CPT];
-  int ph[CPT];
-  auto fetch = [&](int64_t r, int n) {
-    const int64_t In = P.I[n];
-    const float *col = P.UT + P.ut_off[n] + r * In;
-    const int32_t *hn = P.h + d * P.ldh + P.off[n];
-    const int8_t *sn = P.s + d * P.ldh + P.off[n];
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const int64_t i = tid + int64_t(c) * NT;
-      ph[c] = -1;
-      pv[c] = 0.f;
-      if (i < In) {
-        const float v = __ldg(col + i);
-        pv[c] = __ldg(sn + i) < 0 ? -v : v;
-        ph[c] = __ldg(hn + i);
-      }
-    }
-  };
-  fetch(r0, 0);
-  __syncthreads();
-
-  float2 X[EPS][2][RL], p[EPS][2][RL];
-  for (int64_t r = r0; r < r1; ++r) {
-    for (int n = 0; n < N; ++n) {
-#pragma unroll
-      for (int c = 0; c < CPT; ++c)
-        if (unsigned(ph[c]) < unsigned(sb)) atomicAdd(A + ph[c], pv[c]);
-      if (P.I[n] > int64_t(CPT) * NT) {
-        const int64_t In = P.I[n];
-        const float *col = P.UT + P.ut_off[n] + r * In;
-        const int32_t *hn = P.h + d * P.ldh + P.off[n];
-        const int8_t *sn = P.s + d * P.ldh + P.off[n];
-        for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
-          const int hb = __ldg(hn + i);
-          const float v = __ldg(col + i);
-          if (unsigned(hb) < unsigned(sb)) atomicAdd(A + hb, __ldg(sn + i) < 0 ? -v : v);
-        }
-      }
-      if (n + 1 < N)
-        fetch(r, n + 1);
-      else if (r + 1 < r1)
-        fetch(r + 1, 0);
-      __syncthreads();
-      fft_first_pass<L, NT>(A, sb, B);
-      __syncthreads();
-      for (int e = tid; e < sb / 4; e += NT)
-        reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-      fft_middle_passes<L, NT, 1>(B, tws);
-      fft_last_pass_unpack<L, NT>(B, tw, X);
-#pragma unroll
-      for (int e = 0; e < EPS; ++e)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-          for (int q = 0; q < RL; ++q) {
-            if (n == 0) {
-              p[e][b][q] = X[e][b][q];
-            } else {
-              const bool packed = (b == 0 && q == 0 && tid + e * NT == 0);
-              p[e][b][q] = slot_mul(p[e][b][q], X[e][b][q], packed);
-            }
-          }
-    }
-#pragma unroll
-    for (int e = 0; e < EPS; ++e)
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int q = 0; q < RL; ++q) {
-          float2 &acc = accS[((e * 2 + b) * RL + q) * NT + tid];
-          acc = cadd(acc, p[e][b][q]);
-        }
-  }
-
-  // publish the partial spectrum of sketch d
-  float2 *Gd = P.G + d * int64_t(M + 1);
-#pragma unroll
-  for (int e = 0; e < EPS; ++e) {
-    if (LPs::SLOTS % NT != 0 && tid + e * NT >= LPs::SLOTS) continue;
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-      for (int q = 0; q < RL; ++q) {
-        const float2 v = accS[((e * 2 + b) * RL + q) * NT + tid];
-        const int k = last_pass_index<L, NT>(e, b, q);
-        if (k == 0) {
-          atomicAdd(&Gd[0].x, v.x);
-          atomicAdd(&Gd[M].x, v.y);
-        } else {
-          atomicAdd(&Gd[k], v);
-        }
-      }
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) *s_flag = (atomicAdd(&P.tickets[d], 1u) == unsigned(P.groups - 1));
-  __syncthreads();
-  if (*s_flag) {
-    __threadfence();
-    for (int q = tid; q < HALF; q += NT) {
-      float2 Av, Bv;
-      if (q == 0) {
-        Av = make_float2(__ldcg(&Gd[0].x), __ldcg(&Gd[M].x));
-        Bv = __ldcg(&Gd[HALF]);
-      } else {
-        Av = __ldcg(&Gd[q]);
-        Bv = __ldcg(&Gd[M - q]);
-      }
-      pack_pair_conj<L>(B, q, Av, Bv, tw);
-    }
-    __syncthreads();
-    block_fft<L, NT>(B, tw);
-    const float sc = 1.0f / float(M);
-    float *od = P.out + d * P.Jt;
-    const float *Br = reinterpret_cast<const float *>(B);
-    for (int64_t j = tid; j < P.Jt; j += NT) {
-      const float v = Br[real_off(int(j))];
-      od[j] = (j & 1) ? -v * sc : v * sc;
-    }
-    if (tid == 0) P.tickets[d] = 0u;
-  }
-  __syncthreads();
+ClassKernel class_kernel_l(int cpt, int sb) {
+  constexpr int NT = fft_threads(L);
+  ClassKernel k{nullptr, NT, CpSmem<L, NT>::bytes(sb)};
+  if (cpt <= 1)
+    k.fn = reinterpret_cast<const void *>(batch_class_kernel<L, NT, 1>);
+  else if (cpt <= 2)
+    k.fn = reinterpret_cast<const void *>(batch_class_kernel<L, NT, 2>);
+  else
+    k.fn = reinterpret_cast<const void *>(batch_class_kernel<L, NT, 4>);
+  return k;
 }
 
-__global__ void __launch_bounds__(kBatchNT, 1) batch_cp_kernel(const BatchProb *__restrict__ probs,
-                                                            const int4 *__restrict__ items,
-                                                            int nitems, unsigned *queue,
-                                                            const float2 *__restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_item, s_flag;
-  int curL = -1;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = int(atomicAdd(queue, 1u));
-    __syncthreads();
-    const int it = s_item;
-    __syncthreads();
-    if (it >= nitems) break;
-    const int4 w = items[it];
-    const BatchProb &P = probs[w.x];
-    const int64_t r0 = int64_t(w.z) * P.rpi;
-    const int64_t r1 = min(P.R, r0 + P.rpi);
-    const bool fill = P.L != curL;
-    curL = P.L;
-    switch (P.L) {
-#define FCS_BATCH_CASE(K) \
-  case K: batch_item<K>(P, w.y, r0, r1, smem, tw, fill, &s_flag); break;
-      FCS_BATCH_CASE(3) FCS_BATCH_CASE(4) FCS_BATCH_CASE(5) FCS_BATCH_CASE(6)
-      FCS_BATCH_CASE(7) FCS_BATCH_CASE(8) FCS_BATCH_CASE(9) FCS_BATCH_CASE(10)
-      FCS_BATCH_CASE(11) FCS_BATCH_CASE(12) FCS_BATCH_CASE(13)
-#undef FCS_BATCH_CASE
-      default:
-        break;
-    }
-  }
+template <int CPT>
+const void *class13_fn(int ra) {
+  if (ra <= 128) return reinterpret_cast<const void *>(batch_class13_kernel<CPT, 4>);
+  if (ra <= 256) return reinterpret_cast<const void *>(batch_class13_kernel<CPT, 8>);
+  return reinterpret_cast<const void *>(batch_class13_kernel<CPT, 16>);
 }
 
-size_t batch_smem_bytes(int L, int sb) {
+ClassKernel class_kernel(int L, int64_t Imax, int sb) {
+  if (L == wdit::kL) {
+    const int ra = (sb + 31) >> 5;
+    const int cpt = int((Imax + wdit::kNT - 1) / wdit::kNT);
+    const void *fn = cpt <= 1 ? class13_fn<1>(ra) : cpt <= 2 ? class13_fn<2>(ra) : class13_fn<4>(ra);
+    return ClassKernel{fn, wdit::kNT, Cp13Smem::bytes(ra)};
+  }
+  const int nt = fft_threads(L);
+  const int cpt = int((Imax + nt - 1) / nt);
   switch (L) {
-#define FCS_BS_CASE(K) \
-  case K: return BatchSmem<K>::bytes(sb);
-    FCS_BS_CASE(3) FCS_BS_CASE(4) FCS_BS_CASE(5) FCS_BS_CASE(6) FCS_BS_CASE(7)
-    FCS_BS_CASE(8) FCS_BS_CASE(9) FCS_BS_CASE(10) FCS_BS_CASE(11) FCS_BS_CASE(12)
-    FCS_BS_CASE(13)
-#undef FCS_BS_CASE
+#define FCS_CLASS_CASE(K) \
+  case K: return class_kernel_l<K>(cpt, sb);
+    FCS_CLASS_CASE(3) FCS_CLASS_CASE(4) FCS_CLASS_CASE(5) FCS_CLASS_CASE(6)
+    FCS_CLASS_CASE(7) FCS_CLASS_CASE(8) FCS_CLASS_CASE(9) FCS_CLASS_CASE(10)
+    FCS_CLASS_CASE(11) FCS_CLASS_CASE(12)
+#undef FCS_CLASS_CASE
     default:
-      return 0;
+      return ClassKernel{nullptr, 0, 0};
   }
 }
 
@@ -320,7 +234,7 @@ struct HostProb {
   Modes m;
   int L, sb;
   int64_t R, utlen, Imax;
-  bool longp;                  // P > 16384: not for the persistent kernel
+  bool longp;                  // P > 16384: not for the batch kernels
 };
 
 int check_problem(fcs_ctx *ctx, int k, const fcs_cp_problem &q, HostProb *hp) {
@@ -410,8 +324,10 @@ int default_grain(const fcs_ctx *ctx, int nprob, const fcs_cp_problem *q) {
 
 // Lay a batch out at device address `base` (NULL: sizes only).  The device
 // image starts with the descriptors (probs | items | tasks), `desc_bytes`
-// long, whose host copy goes to *host_desc; then the cleared region (queue
-// + tickets | spectrum accumulators) and the transposed factors.
+// long, whose host copy goes to *host_desc; then the cleared region
+// (tickets | spectrum accumulators) and the transposed factors.  Items are
+// grouped into FFT-size classes, largest first, each class's longest items
+// (ranks x modes) first.
 int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, char *base,
                 std::vector<char> *host_desc, BatchBuild *out) {
   std::vector<HostProb> hp(nprob);
@@ -420,7 +336,7 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
     if (rc) return rc;
     if (hp[k].longp)
       return set_error(ctx, FCS_EUNSUPPORTED,
-                       "problem %d: FFT length > %d is not run by the persistent kernel", k,
+                       "problem %d: FFT length > %d is not run by the batch kernels", k,
                        1 << kMaxLog2P);
   }
   std::vector<int4> items;
@@ -435,7 +351,7 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
     probs[k].groups = groups;
     for (int d = 0; d < q[k].D; ++d)
       for (int g = 0; g < groups; ++g) items.push_back(make_int4(k, d, g, 0));
-    g_bytes += up256(sizeof(float2) * size_t(q[k].D) * size_t((1 << hp[k].L) + 1));
+    g_bytes += up256(sizeof(float2) * size_t(q[k].D) * size_t((1 << hp[k].L) + 2));
     t_count += size_t(q[k].D);
     ut_len += size_t(hp[k].utlen);
     ntask += q[k].N;
@@ -449,7 +365,7 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
   const size_t b_probs = up256(sizeof(BatchProb) * nprob);
   const size_t b_items = up256(sizeof(int4) * items.size());
   const size_t b_tasks = up256(sizeof(TransposeTask) * ntask);
-  const size_t b_tick = up256(sizeof(unsigned) * (1 + t_count));
+  const size_t b_tick = up256(sizeof(unsigned) * t_count);
   const size_t b_ut = up256(sizeof(float) * ut_len);
   BatchBuild bb{};
   bb.total = b_probs + b_items + b_tasks + b_tick + g_bytes + b_ut;
@@ -464,11 +380,11 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
     *out = bb;
     return FCS_OK;
   }
-  unsigned *d_queue = reinterpret_cast<unsigned *>(base + bb.clear_off);
+  unsigned *d_tickets = reinterpret_cast<unsigned *>(base + bb.clear_off);
   char *g_base = base + bb.clear_off + b_tick;
   float *ut_base = reinterpret_cast<float *>(g_base + g_bytes);
   std::vector<TransposeTask> tasks;
-  size_t goff = 0, toff = 1, uoff = 0, smem = 0;
+  size_t goff = 0, toff = 0, uoff = 0;
   int64_t tiles = 0;
   for (int k = 0; k < nprob; ++k) {
     BatchProb &P = probs[k];
@@ -487,8 +403,8 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
     P.s = q[k].s;
     P.out = q[k].out;
     P.G = reinterpret_cast<float2 *>(g_base + goff);
-    goff += up256(sizeof(float2) * size_t(P.D) * size_t((1 << P.L) + 1));
-    P.tickets = d_queue + toff;
+    goff += up256(sizeof(float2) * size_t(P.D) * size_t((1 << P.L) + 2));
+    P.tickets = d_tickets + toff;
     toff += size_t(P.D);
     P.UT = ut_base + uoff;
     int64_t local = 0;
@@ -508,7 +424,27 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
       local += P.R * q[k].I[n];
     }
     uoff += size_t(local);
-    smem = std::max(smem, batch_smem_bytes(P.L, P.sb));
+  }
+  // one launch per FFT-size class: prefetch depth and scatter buffer sized
+  // for the class's largest problem
+  for (size_t i = 0; i < items.size();) {
+    const int L = hp[items[i].x].L;
+    size_t j = i;
+    int64_t Imax = 0;
+    int sb = 4;
+    for (; j < items.size() && hp[items[j].x].L == L; ++j) {
+      Imax = std::max(Imax, hp[items[j].x].Imax);
+      sb = std::max(sb, hp[items[j].x].sb);
+    }
+    const ClassKernel ck = class_kernel(L, Imax, sb);
+    if (!ck.fn) return set_error(ctx, FCS_EUNSUPPORTED, "no batch kernel for log2 M = %d", L);
+    if (ck.smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(ck.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(ck.smem));
+      if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(batch class)");
+    }
+    bb.classes.push_back(BatchClass{ck.fn, ck.nt, ck.smem, int(i), int(j - i)});
+    i = j;
   }
   if (tiles > 0x7fffffffLL) return set_error(ctx, FCS_EUNSUPPORTED, "batch too large");
   host_desc->assign(bb.desc_bytes, 0);
@@ -516,17 +452,7 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
   memcpy(host_desc->data() + b_probs, items.data(), sizeof(int4) * items.size());
   memcpy(host_desc->data() + b_probs + b_items, tasks.data(),
          sizeof(TransposeTask) * tasks.size());
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(batch_cp_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(batch)");
-  }
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_cp_kernel, kBatchNT, smem);
-  if (per_sm < 1) per_sm = 1;
   bb.tiles = tiles;
-  bb.smem = smem;
-  bb.grid = std::max(1, std::min(bb.nitems, ctx->sm_count * per_sm));
   *out = bb;
   return FCS_OK;
 }
@@ -540,11 +466,29 @@ int batch_issue(fcs_ctx *ctx, char *base, const BatchBuild &b) {
       reinterpret_cast<const TransposeTask *>(base + b.tasks_off), b.ntasks);
   rc = check_cuda(ctx, cudaGetLastError(), "batch_transpose_kernel");
   if (rc) return rc;
-  batch_cp_kernel<<<b.grid, kBatchNT, b.smem, ctx->stream>>>(
-      reinterpret_cast<const BatchProb *>(base),
-      reinterpret_cast<const int4 *>(base + b.items_off), b.nitems,
-      reinterpret_cast<unsigned *>(base + b.clear_off), ctx->twiddle);
-  return check_cuda(ctx, cudaGetLastError(), "batch_cp_kernel");
+  // the classes as a chain of programmatic dependent launches: each may start
+  // while its predecessor drains (their problems are disjoint), and each
+  // completes after it
+  const BatchProb *probs = reinterpret_cast<const BatchProb *>(base);
+  const float2 *tw = ctx->twiddle;
+  for (size_t c = 0; c < b.classes.size(); ++c) {
+    const BatchClass &k = b.classes[c];
+    const int4 *items = reinterpret_cast<const int4 *>(base + b.items_off) + k.first;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(k.count));
+    cfg.blockDim = dim3(unsigned(k.nt));
+    cfg.dynamicSmemBytes = k.smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = c > 0 ? 1 : 0;
+    void *args[] = {&probs, &items, &tw};
+    rc = check_cuda(ctx, cudaLaunchKernelExC(&cfg, k.fn, args), "batch_class_kernel");
+    if (rc) return rc;
+  }
+  return FCS_OK;
 }
 
 int batch_default_grain(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q) {
@@ -558,7 +502,7 @@ namespace {
 int plan_create(fcs_ctx *ctx, int nprob_all, const fcs_cp_problem *q_all, int grain,
                 fcs_batch_plan **out) {
   *out = nullptr;
-  // problems with P > 16384 run after the persistent kernel, each with the
+  // problems with P > 16384 run after the batch kernels, each with the
   // multi-kernel long-FFT route
   std::vector<fcs_cp_problem> shortp, longp;
   for (int k = 0; k < nprob_all; ++k) {

@@ -8,21 +8,29 @@
 
 namespace fcs {
 
+// One launch of a batch: the items [first, first + count) of one FFT size.
+struct BatchClass {
+  const void *fn;            // kernel
+  int nt;                    // threads per CTA
+  size_t smem;               // dynamic shared memory per CTA
+  int first, count;
+};
+
 // Layout of one batch in device memory (see batch_build).
 struct BatchBuild {
   size_t total = 0;          // device bytes
   size_t desc_bytes = 0;     // descriptor image (host copy -> device base)
   size_t items_off = 0, tasks_off = 0;
   size_t clear_off = 0, clear_bytes = 0;
-  int nitems = 0, ntasks = 0, grid = 0;
+  int nitems = 0, ntasks = 0;
   int64_t tiles = 0;
-  size_t smem = 0;
+  std::vector<BatchClass> classes;
 };
 
 // Lay the batch out at device address `base` (NULL: sizes only, in *out).
 int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, char *base,
                 std::vector<char> *host_desc, BatchBuild *out);
-// Clear accumulators, transpose factors, run the persistent kernel on
+// Clear accumulators, transpose factors, run the class kernels on
 // ctx->stream; the descriptor image must already be at `base`.
 int batch_issue(fcs_ctx *ctx, char *base, const BatchBuild &b);
 // About four work items per SM.

@@ -5,26 +5,19 @@
 //
 // Two kernels.  (1) prep_kernel writes the factor columns contiguously
 // (lambda folded into mode 1) so every column load is coalesced, and clears
-// the spectrum accumulator.  (2) The fused sketch kernel: CTA (g, d) owns sketch d and a contiguous group of
-// ranks.  For each rank and mode it scatters the signed factor column into a
-// compact shared-memory buffer of max_n J_n reals (the Count Sketch of
-// Def. 1; the zero padding up to P is never stored), runs the block real FFT
-// of fcs_fft.cuh whose last pass leaves the half spectrum in registers, and
-// multiplies it into the per-thread mode product; after the last mode the
-// product is added into a shared-memory rank accumulator.  The rank sum thus
-// stays in the frequency domain (linearity moves the paper's sum of inverse
-// transforms inside one inverse transform).  Each CTA adds its partial
-// spectrum into a global accumulator with float2 atomics; the last CTA to
-// finish for sketch d (ticket counter) runs the one inverse real FFT and
-// writes FCS_d.  The next column's factor values and hashes are prefetched
-// into registers while the current column is transformed.  For P = 16384
-// the kernel runs on the warp-DIT engine instead (cp13_kernel): two block
-// barriers per transform, the next column scattered between them.
+// the spectrum accumulator.  (2) The fused sketch kernel: CTA (g, d) owns
+// sketch d and a contiguous group of ranks and runs cp_run (P <= 8192) or
+// cp13_run (P = 16384) of fcs_cp_run.cuh: count sketch, block real FFT, mode
+// product and rank sum in the frequency domain (linearity moves the paper's
+// sum of inverse transforms inside one inverse transform), partial spectrum
+// into a global accumulator, and the one inverse FFT by the CTA that
+// completes sketch d.  Longer transforms go to the two-pass route of
+// fcs_big.cu.
 #include <algorithm>
 #include <cstdarg>
 #include <mutex>
 
-#include "fcs_fft.cuh"
+#include "fcs_cp_run.cuh"
 
 namespace fcs {
 namespace {
@@ -53,371 +46,48 @@ struct TransposeArgs {
   float *UT;
 };
 
-// Shared-memory layout of cp_kernel; every region starts on a 16-byte
-// boundary (the scatter buffer is cleared with float4 stores).
-template <int LOG2M, int NT>
-struct CpSmem {
-  static constexpr size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
-  static constexpr size_t kB = 0;
-  static constexpr size_t kAcc = up16(kB + sizeof(float2) * padded_len(1 << LOG2M));
-  static constexpr size_t kTw =
-      up16(kAcc + sizeof(float2) * LastPass<LOG2M, NT>::NV * NT);
-  static constexpr size_t kA = up16(kTw + sizeof(float2) * plan_twlen(LOG2M));
-  static size_t bytes(int sb) { return kA + sizeof(float) * size_t(sb); }
+// cp_run / cp13_run's accessors over CpArgs (fcs_cp_run.cuh).
+struct CpView {
+  const CpArgs &a;
+  int sb;
+  __device__ __forceinline__ int modes() const { return a.m.N; }
+  __device__ __forceinline__ int64_t dim(int n) const { return a.m.I[n]; }
+  __device__ __forceinline__ const float *column(int n, int64_t r) const {
+    return a.UT + a.ut_off[n] + r * a.m.I[n];
+  }
+  __device__ __forceinline__ const int32_t *hashes(int d, int n) const {
+    return a.h + d * a.m.ldh + a.m.off[n];
+  }
+  __device__ __forceinline__ const int8_t *signs(int d, int n) const {
+    return a.s + d * a.m.ldh + a.m.off[n];
+  }
+  __device__ __forceinline__ int64_t length() const { return a.m.Jt; }
+  __device__ __forceinline__ float *sketch(int d) const { return a.out + d * a.m.Jt; }
+  __device__ __forceinline__ float2 *spectrum() const { return a.G; }
+  __device__ __forceinline__ unsigned *ticket(int d) const { return a.counter + d; }
 };
 
+// CTA (g, d): ranks [g * ranks_per_cta, ...) of sketch d.
 template <int LOG2M, int NT, int CPT>
 __global__ void __launch_bounds__(NT) cp_kernel(CpArgs a, const float2 *__restrict__ tw) {
-  using LPs = LastPass<LOG2M, NT>;
-  constexpr int M = 1 << LOG2M;
-  constexpr int HALF = M / 2;
-  constexpr int RL = LPs::RL, EPS = LPs::EPS, NV = LPs::NV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  using Lay = CpSmem<LOG2M, NT>;
-  float2 *B = reinterpret_cast<float2 *>(smem_raw + Lay::kB);      // padded_len(M)
-  float2 *accS = reinterpret_cast<float2 *>(smem_raw + Lay::kAcc); // NV * NT
-  float2 *tws = reinterpret_cast<float2 *>(smem_raw + Lay::kTw);   // plan_twlen
-  float *A = reinterpret_cast<float *>(smem_raw + Lay::kA);        // a.sb floats
   __shared__ int is_last;
-  const int tid = threadIdx.x;
-  const int d = blockIdx.y;
-  const int N = a.m.N;
   const int64_t r0 = blockIdx.x * a.ranks_per_cta;
   const int64_t r1 = min(a.R, r0 + a.ranks_per_cta);
-  const int sb = a.sb;
-
-  fill_twiddles<LOG2M, NT>(tws, tw);
-  for (int e = tid; e < sb / 4; e += NT) reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) accS[v * NT + tid] = make_float2(0.f, 0.f);
-
-  // prefetched column: signed factor values and hash bins
-  float pv[CPT];
-  int ph[CPT];
-  auto fetch = [&](int64_t r, int n) {
-    const int64_t In = a.m.I[n];
-    const float *col = a.UT + a.ut_off[n] + r * In;
-    const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
-    const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const int64_t i = tid + int64_t(c) * NT;
-      ph[c] = -1;
-      pv[c] = 0.f;
-      if (i < In) {
-        const float v = __ldg(col + i);
-        pv[c] = __ldg(sn + i) < 0 ? -v : v;
-        ph[c] = __ldg(hn + i);
-      }
-    }
-  };
-  fetch(r0, 0);
-  __syncthreads();
-
-  float2 X[EPS][2][RL], p[EPS][2][RL];
-  for (int64_t r = r0; r < r1; ++r) {
-    for (int n = 0; n < N; ++n) {
-#pragma unroll
-      for (int c = 0; c < CPT; ++c)
-        if (unsigned(ph[c]) < unsigned(sb)) atomicAdd(A + ph[c], pv[c]);
-      if (a.m.I[n] > int64_t(CPT) * NT) {
-        // entries beyond the prefetched chunk: load and scatter directly
-        const int64_t In = a.m.I[n];
-        const float *col = a.UT + a.ut_off[n] + r * In;
-        const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
-        const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
-        for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
-          const int hb = __ldg(hn + i);
-          const float v = __ldg(col + i);
-          if (unsigned(hb) < unsigned(sb)) atomicAdd(A + hb, __ldg(sn + i) < 0 ? -v : v);
-        }
-      }
-      // prefetch the next column while this one is transformed
-      if (n + 1 < N)
-        fetch(r, n + 1);
-      else if (r + 1 < r1)
-        fetch(r + 1, 0);
-      __syncthreads();
-      fft_first_pass<LOG2M, NT>(A, sb, B);
-      __syncthreads();
-      for (int e = tid; e < sb / 4; e += NT)
-        reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-      fft_middle_passes<LOG2M, NT, 1>(B, tws);
-      fft_last_pass_unpack<LOG2M, NT>(B, tw, X);
-#pragma unroll
-      for (int e = 0; e < EPS; ++e)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-          for (int q = 0; q < RL; ++q) {
-            if (n == 0) {
-              p[e][b][q] = X[e][b][q];
-            } else {
-              const bool packed = (b == 0 && q == 0 && tid + e * NT == 0);
-              p[e][b][q] = slot_mul(p[e][b][q], X[e][b][q], packed);
-            }
-          }
-    }
-#pragma unroll
-    for (int e = 0; e < EPS; ++e)
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int q = 0; q < RL; ++q) {
-          float2 &acc = accS[((e * 2 + b) * RL + q) * NT + tid];
-          acc = cadd(acc, p[e][b][q]);
-        }
-  }
-
-  // publish the partial spectrum
-  float2 *Gd = a.G + d * int64_t(M + 2);
-#pragma unroll
-  for (int e = 0; e < EPS; ++e) {
-    if (LPs::SLOTS % NT != 0 && tid + e * NT >= LPs::SLOTS) continue;
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-      for (int q = 0; q < RL; ++q) {
-        const float2 v = accS[((e * 2 + b) * RL + q) * NT + tid];
-        const int k = last_pass_index<LOG2M, NT>(e, b, q);
-        if (k == 0) {
-          atomicAdd(&Gd[0].x, v.x);
-          atomicAdd(&Gd[M].x, v.y);
-        } else {
-          atomicAdd(&Gd[k], v);
-        }
-      }
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) is_last = (atomicAdd(&a.counter[d], 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-
-  // last CTA for sketch d: one inverse real FFT of the summed spectrum
-  for (int q = tid; q < HALF; q += NT) {
-    float2 Av, Bv;
-    if (q == 0) {
-      Av = make_float2(__ldcg(&Gd[0].x), __ldcg(&Gd[M].x));
-      Bv = __ldcg(&Gd[HALF]);
-    } else {
-      Av = __ldcg(&Gd[q]);
-      Bv = __ldcg(&Gd[M - q]);
-    }
-    pack_pair_conj<LOG2M>(B, q, Av, Bv, tw);
-  }
-  __syncthreads();
-  block_fft<LOG2M, NT>(B, tw);
-  const float sc = 1.0f / float(M);
-  float *od = a.out + d * a.m.Jt;
-  float *Br = reinterpret_cast<float *>(B);
-  for (int64_t j = tid; j < a.m.Jt; j += NT) {
-    const float v = Br[real_off(int(j))];
-    od[j] = (j & 1) ? -v * sc : v * sc;
-  }
-  if (tid == 0) a.counter[d] = 0u;
+  const CpView view{a, a.sb};
+  cp_run<LOG2M, NT, CPT>(view, blockIdx.y, r0, r1, gridDim.x, smem_raw, tw, &is_last);
 }
 
-// cp_kernel for P = 16384 on the warp-DIT engine (wdit:: in fcs_fft.cuh):
-// the same work split, prefetch, rank accumulation and last-CTA inverse, but
-// two block barriers per transform.  The next column is scattered into the
-// row-wise buffer between them, overlapping step 2 of the current one.
-// RMAX = number of 32-entry blocks per scatter-buffer row (ra <= 32 RMAX).
-struct Cp13Smem {
-  static constexpr size_t kB = 0;                                   // 16 x kRS float2
-  static constexpr size_t kAcc = kB + sizeof(float2) * 16 * wdit::kRS;
-  static constexpr size_t kTw = kAcc + sizeof(float2) * 16 * wdit::kNT;
-  static constexpr size_t kStash = kTw + sizeof(float2) * wdit::kTwLen;
-  static constexpr size_t kA = kStash + sizeof(float2) * 16;
-  static size_t bytes(int ra) { return kA + sizeof(float2) * 16 * size_t(ra); }
-};
-
+// The same for P = 16384 on the warp-DIT engine.  RMAX = number of 32-entry
+// blocks per scatter-buffer row (ra <= 32 RMAX).
 template <int CPT, int RMAX>
 __global__ void __launch_bounds__(wdit::kNT) cp13_kernel(CpArgs a, const float2 *__restrict__ tw) {
-  constexpr int NT = wdit::kNT, M = wdit::kM, HALF = M / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2 *B = reinterpret_cast<float2 *>(smem_raw + Cp13Smem::kB);
-  float4 *acc4 = reinterpret_cast<float4 *>(smem_raw + Cp13Smem::kAcc);   // [8][NT] pairs
-  float2 *tws = reinterpret_cast<float2 *>(smem_raw + Cp13Smem::kTw);
-  float2 *stash = reinterpret_cast<float2 *>(smem_raw + Cp13Smem::kStash);
-  float2 *A2 = reinterpret_cast<float2 *>(smem_raw + Cp13Smem::kA);
-  float *A = reinterpret_cast<float *>(A2);
   __shared__ int is_last;
-  const int tid = threadIdx.x;
-  const int d = blockIdx.y;
-  const int N = a.m.N;
   const int64_t r0 = blockIdx.x * a.ranks_per_cta;
   const int64_t r1 = min(a.R, r0 + a.ranks_per_cta);
-  const int sb = a.sb;
-  const int ra = (sb + 31) >> 5;
-
-  float pv[CPT];
-  int ph[CPT];
-  auto fetch = [&](int64_t r, int n) {
-    const int64_t In = a.m.I[n];
-    const float *col = a.UT + a.ut_off[n] + r * In;
-    const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
-    const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const int64_t i = tid + int64_t(c) * NT;
-      ph[c] = -1;
-      pv[c] = 0.f;
-      if (i < In) {
-        const float v = __ldg(col + i);
-        pv[c] = __ldg(sn + i) < 0 ? -v : v;
-        ph[c] = __ldg(hn + i);
-      }
-    }
-  };
-  // scatter the fetched column (and, for I_n > CPT NT, the rest of it)
-  auto scatter = [&](int64_t r, int n) {
-#pragma unroll
-    for (int c = 0; c < CPT; ++c)
-      if (unsigned(ph[c]) < unsigned(sb)) atomicAdd(A + wdit::a_index(ph[c], ra), pv[c]);
-    const int64_t In = a.m.I[n];
-    if (In > int64_t(CPT) * NT) {
-      const float *col = a.UT + a.ut_off[n] + r * In;
-      const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
-      const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
-      for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
-        const int hb = __ldg(hn + i);
-        const float v = __ldg(col + i);
-        if (unsigned(hb) < unsigned(sb))
-          atomicAdd(A + wdit::a_index(hb, ra), __ldg(sn + i) < 0 ? -v : v);
-      }
-    }
-  };
-  // the first column's loads and the twiddle loads overlap
-  fetch(r0, 0);
-  wdit::fill_twiddles(tws, tw);
-  for (int e = tid; e < 16 * ra; e += NT) A2[e] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) acc4[q * NT + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncthreads();
-  scatter(r0, 0);
-  __syncthreads();
-
-  float2 p[16];
-  for (int64_t r = r0; r < r1; ++r) {
-    for (int n = 0; n < N; ++n) {
-      // the scatter buffer holds column (r, n); fetch the next one
-      int64_t rn = r;
-      int nn = n + 1;
-      if (nn == N) {
-        nn = 0;
-        ++rn;
-      }
-      const bool more = rn < r1;
-      if (more) fetch(rn, nn);
-      wdit::step1<RMAX>(A2, ra, B, tws);
-      __syncthreads();
-      // warps 0-7 scatter the next column before step 2, warps 8-15 after it,
-      // so each scheduler overlaps the atomics' latency with step-2 work
-      const bool early = tid < NT / 2;
-      if (more && early) scatter(rn, nn);
-      float2 v[16];
-      wdit::step2(B, tws, stash, v);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (n == 0)
-          p[j] = v[j];
-        else
-          p[j] = slot_mul(p[j], v[j], tid == 0 && j == 0);
-      }
-      if (n == N - 1) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          float4 &acc = acc4[q * NT + tid];
-          float4 x = acc;
-          x.x += p[2 * q].x;
-          x.y += p[2 * q].y;
-          x.z += p[2 * q + 1].x;
-          x.w += p[2 * q + 1].y;
-          acc = x;
-        }
-      }
-      if (more && !early) scatter(rn, nn);
-      __syncthreads();
-    }
-  }
-
-  // publish the partial spectrum as 16-byte atomics over bin pairs (k, k+1);
-  // value j of thread t is 2^N X[spectrum_index(q2(t), j)]
-  float2 *Gd = a.G + d * int64_t(M + 2);
-  const float2 *accv = reinterpret_cast<const float2 *>(acc4);
-  auto acc_at = [&](int k) -> float2 {       // accumulated value of bin k (k < M)
-    const int jj = k >> 9, c = k & 511;
-    const int q2 = jj < 8 ? c : wdit::q2_partner(c);
-    const int u = q2 <= 256 ? (q2 == 256 ? 0 : q2) : 512 - q2;
-    const int e = q2 >= 256 ? 1 : 0;
-    const int t = ((u >> 4) << 5) | (e << 4) | (u & 15);
-    return accv[((jj >> 1) * NT + t) * 2 + (jj & 1)];
-  };
-  for (int f = tid; f < M / 2; f += NT) {
-    const float2 x0 = acc_at(2 * f), x1 = acc_at(2 * f + 1);
-    if (f == 0) {
-      atomicAdd(&Gd[M].x, x0.y);            // bin M (packed with bin 0)
-      atomicAdd(reinterpret_cast<float4 *>(Gd), make_float4(x0.x, 0.f, x1.x, x1.y));
-    } else {
-      atomicAdd(reinterpret_cast<float4 *>(Gd) + f, make_float4(x0.x, x0.y, x1.x, x1.y));
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) is_last = (atomicAdd(&a.counter[d], 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-
-  // last CTA for sketch d: one inverse real FFT of the summed spectrum on the
-  // same engine.  The conj-packed sequence goes row-wise (ra = 512) into the
-  // accumulator region; a forward complex FFT, conj and scaling give FCS_d.
-  float2 *Z2 = reinterpret_cast<float2 *>(acc4);
-  {
-    // all (coalesced) loads first: one L2 round trip
-    constexpr int PER = HALF / NT;
-    float2 Av[PER], Bv[PER], Wv[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int q = k * NT + tid;
-      if (q == 0) {
-        Av[k] = make_float2(__ldcg(&Gd[0].x), __ldcg(&Gd[M].x));
-        Bv[k] = __ldcg(&Gd[HALF]);
-        Wv[k] = make_float2(1.f, 0.f);
-      } else {
-        Av[k] = __ldcg(&Gd[q]);
-        Bv[k] = __ldcg(&Gd[M - q]);
-        Wv[k] = __ldg(&tw[q << (kLogTwN - wdit::kL - 1)]);   // W_P^q
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int q = k * NT + tid;
-      float2 cq, cm;
-      pack_pair_conj_values_w(q, Av[k], Bv[k], Wv[k], cq, cm);
-      Z2[wdit::row_pos_swz(q)] = cq;
-      Z2[wdit::row_pos_swz(q ? M - q : HALF)] = cm;
-    }
-  }
-  __syncthreads();
-  wdit::step1<16, true>(Z2, 512, B, tws);
-  __syncthreads();
-  float2 v[16];
-  wdit::step2_complex(B, tws, v);                   // v[q1] = Z[q2 + 512 q1]
-  // 1/M of the inverse and 2^-N for the doubled unpack of every mode
-  const float sc = 1.0f / float(int64_t(M) << N);
-  float *od = a.out + d * a.m.Jt;
-  const int64_t Jt = a.m.Jt;
-  const int q2 = wdit::q2_of(tid);
-#pragma unroll
-  for (int q1 = 0; q1 < 16; ++q1) {
-    const int64_t m = q2 + 512 * q1;
-    if (2 * m < Jt) od[2 * m] = v[q1].x * sc;
-    if (2 * m + 1 < Jt) od[2 * m + 1] = -v[q1].y * sc;
-  }
-  if (tid == 0) a.counter[d] = 0u;
+  const CpView view{a, a.sb};
+  cp13_run<CPT, RMAX>(view, blockIdx.y, r0, r1, gridDim.x, smem_raw, tw, &is_last);
 }
 
 // prep_kernel: in one launch, the factor transpose in 32 x 32 tiles,

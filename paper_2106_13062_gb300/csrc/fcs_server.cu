@@ -10,7 +10,7 @@
 //   2. when a stream is free, admits queued requests in FIFO order while
 //      in-flight slots, device arena memory and pinned staging memory allow,
 //      and issues them as one round on that stream: host->device copies,
-//      hash generation, ONE batched persistent launch for all admitted CP
+//      hash generation, ONE batched launch chain for all admitted CP
 //      requests (fcs_batch building blocks), the contractions, and
 //      device->host copies, closed by an event;
 //   3. otherwise sleeps on a condition variable (woken by submit) for at most
@@ -133,6 +133,7 @@ struct Round {
   size_t pin_off = 0, pin_bytes = 0;     // pinned block for descriptors
   bool busy = false;
   int status = FCS_OK;
+  int batch_launches = 0;                // kernels of the round's batched CP launch
 };
 
 int64_t jtilde_of(int N, const int32_t *J) {
@@ -164,6 +165,7 @@ struct fcs_server {
   // statistics
   std::vector<double> lat;
   int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, nrounds = 0, sketches = 0;
+  int64_t batch_launches = 0;
   Clock::time_point t_first, t_last;
   bool any_submit = false;
 };
@@ -380,7 +382,7 @@ int issue_round(fcs_server *S, int si, std::vector<Req *> &reqs, Round &rd) {
       p.ldh = 0;
       p.out = q->dout;
       if (q->Jt > (int64_t(1) << fcs::kMaxLog2P)) {
-        // too long for the persistent kernel: its own (multi-kernel) launch
+        // too long for the batch kernels: its own (multi-kernel) launch
         rc = fcs_sketch_cp(ctx, p.N, p.I, p.J, p.R, p.D, p.U, p.ldU, p.lambda, p.h, p.s, p.ldh,
                            p.out);
         if (rc) return rc;
@@ -433,6 +435,7 @@ int issue_round(fcs_server *S, int si, std::vector<Req *> &reqs, Round &rd) {
         return FCS_ECUDA;
       rc = fcs::batch_issue(ctx, pb, bb);
       if (rc) return rc;
+      rd.batch_launches = 1 + int(bb.classes.size());
     } else {
       // no room for a batch plan right now: one launch per request instead
       for (const fcs_cp_problem &p : probs) {
@@ -508,11 +511,13 @@ void worker_loop(fcs_server *S) {
           rd.busy = true;
           rd.reqs = got;
           rd.status = FCS_OK;
+          rd.batch_launches = 0;
           S->nrounds++;
           lk.unlock();
           int rc = issue_round(S, si, got, rd);
           cudaEventRecord(rd.done, S->streams[si]);
           lk.lock();
+          S->batch_launches += rd.batch_launches;
           if (rc != FCS_OK) rd.status = rc;
           progress = true;
         }
@@ -761,6 +766,7 @@ extern "C" int fcs_server_stats(fcs_server *S, fcs_stats *out) {
   out->failed = S->failed;
   out->cancelled = S->cancelled;
   out->rounds = S->nrounds;
+  out->batch_launches = S->batch_launches;
   out->sketches = S->sketches;
   out->max_inflight_seen = S->max_inflight_seen;
   out->arena_used = S->darena.used();
@@ -786,6 +792,7 @@ extern "C" int fcs_server_reset_stats(fcs_server *S) {
   std::lock_guard<std::mutex> lk(S->mu);
   S->lat.clear();
   S->submitted = S->completed = S->failed = S->cancelled = S->nrounds = S->sketches = 0;
+  S->batch_launches = 0;
   S->max_inflight_seen = S->inflight;
   S->any_submit = false;
   return FCS_OK;
