@@ -10,6 +10,9 @@
 // hash of the leading modes is computed once per row and sketch.
 #include "fcs_internal.cuh"
 
+#include <cfloat>
+#include <type_traits>
+
 namespace fcs {
 namespace {
 
@@ -143,23 +146,75 @@ __global__ void __launch_bounds__(1024) dense_kernel(DenseArgs a) {
 // Row-chunk kernel (contiguous last mode, J_{N-1} < 2^15): warp w owns a
 // fixed chunk of 256 consecutive last-mode indices (two float4 per lane) and
 // walks the rows i_1..i_{N-1} of its batch item.  Because the chunk never
-// changes, the lane's last-mode hash/sign entries for all D sketches stay in
-// registers (16-bit packed pairs) for the whole kernel; only the leading
-// modes' entries are read from shared memory, once per row and sketch.  The
-// next row's values are prefetched while the current row is scattered.
-template <int D, int NT>
+// changes, the lane's last-mode bin offsets (16-bit pairs) and signs (one bit
+// each) for all D sketches stay in registers for the whole kernel; the
+// leading modes' partial hash and sign are the same for the whole warp, read
+// from shared memory once per row and sketch.  The next row's values are
+// prefetched while the current row is scattered.
+//
+// Accumulation is exact integer fixed point: shared-memory FP32 atomics are a
+// compare-and-swap loop (about 6x slower than a 32-bit integer atomic add), so
+// every entry x is rounded once to xi = rint(x / q) with a power-of-two step
+// q = 2^(E-25) per CTA, where 2^E bounds the magnitudes of a sample (the first
+// row of every warp), and the D signed copies of xi are added with int32
+// atomics.  Integer sums do not depend on the order of the adds.  Three cases
+// leave the fast path, each exactly:
+//  * outliers (|x| >= ~2^31 q, NaN, Inf) are added in FP32 straight into the
+//    output sketch with global atomics;
+//  * a bin whose int32 sum wraps adds the carry, +-2^32 q (a power of two),
+//    to the output the same way, so bins are effectively 64-bit;
+//  * if the rounding error of the CTA, whose expected L2 norm is
+//    q sqrt(n/12) for n rounded entries, exceeds 1e-7 of the CTA's
+//    ||x||_2 (data with a large dynamic range), the CTA re-reads its rows and
+//    adds the exact remainders x - q xi with FP32 shared atomics.
+// A CTA whose sample is all zeros or outside 2^-100..2^100 accumulates in FP32.
+// The bins are flushed to the output as FP32 (q xi_sum, one rounding).
+// Hash values outside [0, J_n) are skipped; a CTA that finds one in its
+// tables takes the checked (slower) scatter for every row.
+// NL = number of leading modes (N - 1) when known at compile time, -1 for the
+// general case (N - 1 <= kMaxN - 1, checked at run time).
+template <int NT, int NL>
 __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, int cpr,
-                                                        int64_t warps_used) {
+                                                        int64_t warps_used, int DC) {
+  constexpr int NLMAX = NL >= 0 ? NL : kMaxN - 1;
+  auto leading = [&](int n) { return n < NLMAX && (NL >= 0 || n < a.m.N - 1); };
+  // this CTA handles sketches d0 .. d0 + nd - 1 (nd <= DC); d below is local
+  const int d0 = blockIdx.z * DC;
+  const int nd = min(DC, a.D - d0);
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int s_max;            // sample max |x|, FP32 bits
+  __shared__ float s_sumsq;
+  __shared__ unsigned long long s_nfx;
+  __shared__ int s_bad;                     // some hash value outside [0, J_n)
   const int N = a.m.N;
   const int64_t Jt = a.m.Jt;
-  int32_t *tab = reinterpret_cast<int32_t *>(smem);       // [D][totL] leading modes
-  float *bins = reinterpret_cast<float *>(tab + D * totL);  // [D][Jt]
-  for (int e = threadIdx.x; e < D * totL; e += NT) {
-    const int d = e / totL;
-    tab[e] = packed_entry(a, d, e - d * totL);
+  uint32_t *ltab = reinterpret_cast<uint32_t *>(smem);     // [nd][cpr][32][4] last mode
+  int32_t *tab = reinterpret_cast<int32_t *>(ltab + DC * cpr * 128);   // [nd][totL] leading
+  int32_t *ibins = tab + DC * totL;                        // [nd][Jt] int32 (or FP32)
+  float *fbins = reinterpret_cast<float *>(ibins);
+  if (threadIdx.x == 0) {
+    s_max = 0u;
+    s_sumsq = 0.f;
+    s_nfx = 0ull;
+    s_bad = 0;
   }
-  for (int64_t e = threadIdx.x; e < D * Jt; e += NT) bins[e] = 0.f;
+  __syncthreads();
+  {
+    int bad = 0;
+    for (int e = threadIdx.x; e < nd * totL; e += NT) {
+      const int d = e / totL;
+      const int k = e - d * totL;
+      const int32_t t = packed_entry(a, d0 + d, k);
+      int n = 0;
+#pragma unroll
+      for (int m = 1; m < kMaxN - 1; ++m)
+        if (m < N - 1 && k >= a.m.off[m]) n = m;
+      bad |= int(unsigned(t >> 1) >= unsigned(a.m.J[n]));
+      tab[e] = t;
+    }
+    if (bad) s_bad = 1;
+  }
+  for (int64_t e = threadIdx.x; e < nd * Jt; e += NT) ibins[e] = 0;
 
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * int64_t(NT) + threadIdx.x) >> 5;
@@ -167,25 +222,30 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
   const int64_t rstride = warps_used / cpr;
   const int64_t i0 = int64_t(c) * 256 + lane * 4;      // segment s starts at i0 + 128 s
   const bool act0 = i0 < a.L, act1 = i0 + 128 < a.L;
-  // last-mode entries: word[d][m] packs elements 2m (low) and 2m+1 (high)
-  uint32_t tl[D][4];
+  // last-mode tables in shared memory, one 16-byte word per (sketch, chunk,
+  // lane): eight 16-bit entries (offset in bits 0..14, sign in bit 15) for
+  // the lane's elements e = 0..7, last-mode index i0 + (e / 4) * 128 + e % 4.
+  // Absent elements (past the end of the mode) get a distinct in-range
+  // offset and value 0, so they add nothing and never collide.
   {
     const int64_t offl = a.m.off[N - 1];
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        uint32_t w = 0;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int e = 2 * m + q;                      // element: segment e/4, lane slot e%4
-          const int64_t i = i0 + (e >> 2) * 128 + (e & 3);
-          if (i < a.L) w |= uint32_t(packed_entry(a, d, int(offl + i)) & 0xffff) << (16 * q);
-        }
-        tl[d][m] = w;
+    const uint32_t JL = uint32_t(a.m.J[N - 1]);
+    int bad = 0;
+    for (int k = threadIdx.x; k < nd * cpr * 32 * 8; k += NT) {
+      const int e = k & 7, ln = (k >> 3) & 31;
+      const int cc = (k >> 8) % cpr, d = (k >> 8) / cpr;
+      const int64_t i = int64_t(cc) * 256 + ln * 4 + (e >> 2) * 128 + (e & 3);
+      uint32_t t16 = uint32_t(ln) % JL;
+      if (i < a.L) {
+        const int32_t t = packed_entry(a, d0 + d, int(offl + i));
+        const uint32_t hv = uint32_t(t >> 1);
+        bad |= int(hv >= JL);
+        t16 = (hv < JL ? hv : 0u) | (uint32_t(t & 1) << 15);
       }
+      reinterpret_cast<uint16_t *>(ltab)[k] = uint16_t(t16);
+    }
+    if (bad) s_bad = 1;
   }
-  __syncthreads();
 
   const int b = blockIdx.y;
   const float *Tb = a.T + b * a.tbs;
@@ -195,8 +255,8 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
     uint32_t rr = uint32_t(row);
     int64_t addr = 0;
 #pragma unroll
-    for (int n = kMaxN - 2; n >= 0; --n) {
-      if (n < N - 1) {
+    for (int n = NLMAX - 1; n >= 0; --n) {
+      if (leading(n)) {
         const uint32_t In = uint32_t(a.m.I[n]);
         const uint32_t q = rr / In;
         idx[n] = int(rr - q * In);
@@ -212,47 +272,205 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
     x1 = act1 ? __ldcs(reinterpret_cast<const float4 *>(Tb + addr + i0 + 128))
               : make_float4(0.f, 0.f, 0.f, 0.f);
   };
-
-  int64_t row = gw / cpr;
   const bool working = gw < warps_used;
-  int idx[kMaxN], nidx[kMaxN];
+  const int64_t row0 = gw / cpr;
+
+  // ---- scale from the sample: the first row of every warp
+  {
+    float m = 0.f;
+    if (working && row0 < a.rows) {
+      int idx[kMaxN];
+      float4 x0, x1;
+      load(row_addr(row0, idx), x0, x1);
+      const float v[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-  for (int n = 0; n < kMaxN; ++n) idx[n] = nidx[n] = 0;
-  float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
-  if (working && row < a.rows) load(row_addr(row, nidx), n0, n1);
-  for (; working && row < a.rows; row += rstride) {
+      for (int e = 0; e < 8; ++e)
+        if (fabsf(v[e]) <= FLT_MAX) m = fmaxf(m, fabsf(v[e]));
+    }
 #pragma unroll
-    for (int n = 0; n < kMaxN; ++n) idx[n] = nidx[n];
-    const float v[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
-    if (row + rstride < a.rows) load(row_addr(row + rstride, nidx), n0, n1);
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m > 0.f) atomicMax(&s_max, __float_as_uint(m));
+  }
+  __syncthreads();
+  const bool tables_ok = s_bad == 0;
+  int E = 0;
+  const float smax = __uint_as_float(s_max);
+  frexpf(smax, &E);                        // smax < 2^E
+  const bool fx = smax > 0.f && E > -100 && E < 100;
+  const float q = fx ? ldexpf(1.f, E - 25) : 1.f;        // fixed-point step
+  const float inv_q = fx ? ldexpf(1.f, 25 - E) : 1.f;
+  const float carry = fx ? ldexpf(1.f, E + 7) : 0.f;     // 2^32 q
+
+  // Fast scatter of one row into sketch d: eight int32 adds issued back to
+  // back, then one test for a wrap among them.  LNEG is the leading modes'
+  // sign, uniform across the warp.
+  auto scatter_fast = [&](auto lneg_c, int d, int base, const int *xi, const int *nxi) {
+    constexpr bool LNEG = decltype(lneg_c)::value;
+    const uint4 tw = reinterpret_cast<const uint4 *>(ltab)[(d * cpr + c) * 32 + lane];
+    const uint32_t w[4] = {tw.x, tw.y, tw.z, tw.w};
+    int32_t *bb = ibins + d * Jt + base;
+    int val[8], old[8];
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      int base = 0, neg = 0;
+    for (int e = 0; e < 8; ++e) {
+      const uint32_t t = (e & 1) ? (w[e >> 1] >> 16) : w[e >> 1];
+      const bool sneg = ((t >> 15) & 1u) != 0;
+      val[e] = (sneg != LNEG) ? nxi[e] : xi[e];
+      old[e] = atomicAdd(bb + (t & 0x7fffu), val[e]);
+    }
+    int flag = 0;
 #pragma unroll
-      for (int n = 0; n < kMaxN - 1; ++n) {
-        if (n < N - 1) {
-          const int32_t t = tab[d * totL + int(a.m.off[n] + idx[n])];
-          base += t >> 1;
-          neg ^= t & 1;
-        }
-      }
-      float *bd = bins + d * Jt;
+    for (int e = 0; e < 8; ++e) {
+      const int nw = int(unsigned(old[e]) + unsigned(val[e]));
+      flag |= (old[e] ^ nw) & (val[e] ^ nw);
+    }
+    if (flag < 0) {                                    // rare: carry out of a bin
+      float *od = outb + (d0 + d) * Jt + base;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        if ((e < 4) ? act0 : act1) {
-          const uint32_t t = (tl[d][e >> 1] >> (16 * (e & 1))) & 0xffffu;
-          const int bin = base + int(t >> 1);
-          const float x = ((uint32_t(neg) ^ t) & 1u) ? -v[e] : v[e];
-          if (unsigned(bin) < unsigned(Jt)) atomicAdd(bd + bin, x);
+        const uint32_t t = (e & 1) ? (w[e >> 1] >> 16) : w[e >> 1];
+        const int nw = int(unsigned(old[e]) + unsigned(val[e]));
+        if (((old[e] ^ nw) & (val[e] ^ nw)) < 0)
+          atomicAdd(od + (t & 0x7fffu), val[e] > 0 ? carry : -carry);
+      }
+    }
+  };
+
+  // mode 0: fixed point (+ outliers, carries); 1: FP32 remainders x - q xi
+  // of the fixed-point entries; 2: plain FP32 accumulation.
+  float sumsq = 0.f;
+  unsigned nfx = 0;
+  auto run_rows = [&](auto mode_c) {
+    constexpr int MODE = decltype(mode_c)::value;
+    int64_t row = row0;
+    int idx[kMaxN], nidx[kMaxN];
+#pragma unroll
+    for (int n = 0; n < kMaxN; ++n) idx[n] = nidx[n] = 0;
+    float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+    if (working && row < a.rows) load(row_addr(row, nidx), n0, n1);
+    for (; working && row < a.rows; row += rstride) {
+#pragma unroll
+      for (int n = 0; n < kMaxN; ++n) idx[n] = nidx[n];
+      const float v[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+      if (row + rstride < a.rows) load(row_addr(row + rstride, nidx), n0, n1);
+      int xi[8], nxi[8];
+      float rv[8];
+      unsigned fastm = 0;          // bit e: entry e goes through the integer path
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const float u = v[e] * inv_q;
+        const bool fast = fabsf(u) < 2147483520.f;       // 2^31 - 2^7; false for NaN
+        xi[e] = fast ? __float2int_rn(u) : 0;
+        nxi[e] = -xi[e];
+        fastm |= unsigned(fast) << e;
+        if (MODE == 0) {
+          sumsq = fmaf(u, u, sumsq);       // in units of q^2
+          nfx += unsigned(fast);
+        }
+        rv[e] = MODE == 1 ? (fast ? fmaf(-q, __int2float_rn(xi[e]), v[e]) : 0.f) : v[e];
+      }
+      const bool fast_row =
+          MODE == 0 && tables_ok && __all_sync(0xffffffffu, fastm == 0xffu);
+      if (fast_row) {
+#pragma unroll 1
+        for (int d = 0; d < nd; ++d) {
+          int base = 0, neg = 0;
+#pragma unroll
+          for (int n = 0; n < NLMAX; ++n) {
+            if (leading(n)) {
+              const int32_t t = tab[d * totL + int(a.m.off[n] + idx[n])];
+              base += t >> 1;
+              neg ^= t & 1;
+            }
+          }
+          if (neg)
+            scatter_fast(std::true_type(), d, base, xi, nxi);
+          else
+            scatter_fast(std::false_type(), d, base, xi, nxi);
+        }
+        continue;
+      }
+      // checked scatter (bad hash values, outliers, FP32 modes): the tables
+      // are re-read from global memory and every index is checked
+#pragma unroll 1
+      for (int d = 0; d < nd; ++d) {
+        int base = 0, neg = 0;
+        bool row_ok = true;
+#pragma unroll
+        for (int n = 0; n < NLMAX; ++n) {
+          if (leading(n)) {
+            const int32_t t = tab[d * totL + int(a.m.off[n] + idx[n])];
+            base += t >> 1;
+            neg ^= t & 1;
+            row_ok = row_ok && unsigned(t >> 1) < unsigned(a.m.J[n]);
+          }
+        }
+        if (!row_ok) continue;
+        int32_t *bi = ibins + d * Jt + base;
+        float *bf = fbins + d * Jt + base;
+        float *od = outb + (d0 + d) * Jt + base;
+        const uint32_t JL = uint32_t(a.m.J[N - 1]);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          if (!((e < 4) ? act0 : act1)) continue;
+          const int64_t il = i0 + (e >> 2) * 128 + (e & 3);
+          const int32_t t = packed_entry(a, d0 + d, int(a.m.off[N - 1] + il));
+          const uint32_t off = uint32_t(t >> 1);
+          if (off >= JL) continue;
+          const bool sneg = ((t & 1) != 0) != (neg != 0);
+          if (MODE == 0) {
+            if ((fastm >> e) & 1u) {
+              const int val = sneg ? -xi[e] : xi[e];
+              const int old = atomicAdd(bi + off, val);
+              const int nw = int(unsigned(old) + unsigned(val));
+              if (((old ^ nw) & (val ^ nw)) < 0) atomicAdd(od + off, val > 0 ? carry : -carry);
+            } else {
+              atomicAdd(od + off, sneg ? -v[e] : v[e]);   // outlier, exact FP32
+            }
+          } else if (MODE == 2 || ((fastm >> e) & 1u)) {
+            atomicAdd(bf + off, sneg ? -rv[e] : rv[e]);
+          }
         }
       }
     }
+  };
+  auto flush_float = [&]() {
+    for (int64_t e = threadIdx.x; e < nd * Jt; e += NT) {
+      const float x = fbins[e];
+      if (x != 0.f) atomicAdd(&outb[d0 * Jt + e], x);
+    }
+  };
+
+  if (!fx) {                          // this CTA accumulates in FP32
+    run_rows(std::integral_constant<int, 2>());
+    __syncthreads();
+    flush_float();
+    return;
+  }
+  run_rows(std::integral_constant<int, 0>());
+  // CTA totals for the rounding-error test
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    sumsq += __shfl_xor_sync(0xffffffffu, sumsq, o);
+    nfx += __shfl_xor_sync(0xffffffffu, nfx, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&s_sumsq, sumsq);
+    atomicAdd(&s_nfx, (unsigned long long)nfx);
   }
   __syncthreads();
-  for (int64_t e = threadIdx.x; e < D * Jt; e += NT) {
-    const float x = bins[e];
-    if (x != 0.f) atomicAdd(&outb[e], x);
+  for (int64_t e = threadIdx.x; e < nd * Jt; e += NT) {
+    const int32_t x = ibins[e];
+    if (x != 0) atomicAdd(&outb[d0 * Jt + e], __int2float_rn(x) * q);
   }
+  // expected squared rounding error n q^2 / 12 against (1e-7 ||x||)^2, in
+  // units of q^2 (the test is uniform across the CTA)
+  if (!(float(s_nfx) * (1.f / 12.f) > 1e-14f * s_sumsq)) return;
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < nd * Jt; e += NT) fbins[e] = 0.f;
+  __syncthreads();
+  run_rows(std::integral_constant<int, 1>());
+  __syncthreads();
+  flush_float();
 }
 
 }  // namespace
@@ -341,11 +559,20 @@ extern "C" int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
     kern<<<dim3(unsigned(per_item), unsigned(nbatch)), threads, sm, ctx->stream>>>(a);
     return check_cuda(ctx, cudaGetLastError(), "dense_kernel");
   };
-  // row-chunk kernel: contiguous last mode, 16-bit last-mode entries
+  // row-chunk kernel: contiguous last mode, 15-bit last-mode offsets.  The D
+  // sketches are split into the fewest groups (one per blockIdx.z) whose
+  // bins and tables fit in shared memory; each group reads T once.
   int64_t totL = tot - host_I[N - 1];
-  const size_t smem_rows = size_t(D) * (size_t(totL) + size_t(Jt)) * 4;
+  const int cpr_rows = int((host_I[N - 1] + 255) / 256);
+  auto rows_smem = [&](int dc) {
+    return size_t(dc) * (size_t(totL) + size_t(Jt)) * 4 + size_t(dc) * size_t(cpr_rows) * 512;
+  };
+  int ngroups = 1;
+  while (ngroups < D && rows_smem((D + ngroups - 1) / ngroups) > 200 * 1024) ++ngroups;
+  const int DC = (D + ngroups - 1) / ngroups;
+  const size_t smem_rows = rows_smem(DC);
   if (vec && host_J[N - 1] <= 32767 && smem_rows <= 200 * 1024 && a.rows < (int64_t(1) << 31)) {
-    const int cpr = int((a.L + 255) / 256);
+    const int cpr = cpr_rows;
     auto launch_rows = [&](auto kern, int nt) -> int {
       if (smem_rows > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -355,7 +582,8 @@ extern "C" int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
       int per_sm = 1;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem_rows);
       if (per_sm < 1) per_sm = 1;
-      int64_t per_item = (int64_t(ctx->sm_count) * per_sm + nbatch - 1) / nbatch;
+      const int64_t slots = int64_t(nbatch) * ngroups;
+      int64_t per_item = (int64_t(ctx->sm_count) * per_sm + slots - 1) / slots;
       // no more warps than (rows x chunks) work units
       const int64_t need_warps = a.rows * cpr;
       const int64_t need = (need_warps * 32 + nt - 1) / nt;
@@ -367,23 +595,16 @@ extern "C" int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
         per_item = (int64_t(cpr) * 32 + nt - 1) / nt;
         used = cpr;
       }
-      kern<<<dim3(unsigned(per_item), unsigned(nbatch)), nt, smem_rows, ctx->stream>>>(
-          a, int(totL), cpr, used);
+      kern<<<dim3(unsigned(per_item), unsigned(nbatch), unsigned(ngroups)), nt, smem_rows,
+             ctx->stream>>>(a, int(totL), cpr, used, DC);
       return check_cuda(ctx, cudaGetLastError(), "dense_rows_kernel");
     };
-    switch (D) {
-#define FCS_DR_CASE(K)                                          \
-  case K: {                                                     \
-    constexpr int kNT = (K <= 4) ? 1024 : 512;                  \
-    return launch_rows(dense_rows_kernel<K, kNT>, kNT);         \
-  }
-      FCS_DR_CASE(1) FCS_DR_CASE(2) FCS_DR_CASE(3) FCS_DR_CASE(4) FCS_DR_CASE(5)
-      FCS_DR_CASE(6) FCS_DR_CASE(7) FCS_DR_CASE(8) FCS_DR_CASE(9) FCS_DR_CASE(10)
-      FCS_DR_CASE(11) FCS_DR_CASE(12) FCS_DR_CASE(13) FCS_DR_CASE(14) FCS_DR_CASE(15)
-      FCS_DR_CASE(16)
-#undef FCS_DR_CASE
-      default:
-        break;
+    switch (N - 1) {
+      case 0: return launch_rows(dense_rows_kernel<512, 0>, 512);
+      case 1: return launch_rows(dense_rows_kernel<512, 1>, 512);
+      case 2: return launch_rows(dense_rows_kernel<512, 2>, 512);
+      case 3: return launch_rows(dense_rows_kernel<512, 3>, 512);
+      default: return launch_rows(dense_rows_kernel<512, -1>, 512);
     }
   }
   if (vec)
