@@ -159,10 +159,13 @@ __global__ void __launch_bounds__(1024) dense_kernel(DenseArgs a) {
 // row of every warp), and the D signed copies of xi are added with int32
 // atomics.  Integer sums do not depend on the order of the adds.  Three cases
 // leave the fast path, each exactly:
-//  * outliers (|x| >= ~2^31 q, NaN, Inf) are added in FP32 straight into the
+//  * outliers (|x| >= ~2^30 q, NaN, Inf) are added in FP32 straight into the
 //    output sketch with global atomics;
 //  * a bin whose int32 sum wraps adds the carry, +-2^32 q (a power of two),
-//    to the output the same way, so bins are effectively 64-bit;
+//    to the output the same way, so bins are effectively 64-bit.  Every add
+//    returns the bin's old value; an add of |xi| < 2^30 to a bin below 2^30
+//    in magnitude cannot wrap, so only adds that saw a larger old value are
+//    examined for a wrap;
 //  * if the rounding error of the CTA, whose expected L2 norm is
 //    q sqrt(n/12) for n rounded entries, exceeds 1e-7 of the CTA's
 //    ||x||_2 (data with a large dynamic range), the CTA re-reads its rows and
@@ -189,7 +192,8 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
   const int N = a.m.N;
   const int64_t Jt = a.m.Jt;
   uint32_t *ltab = reinterpret_cast<uint32_t *>(smem);     // [nd][cpr][32][4] last mode
-  int32_t *tab = reinterpret_cast<int32_t *>(ltab + DC * cpr * 128);   // [nd][totL] leading
+  uint32_t *lsg = ltab + DC * cpr * 128;                  // [nd][cpr][32] sign masks
+  int32_t *tab = reinterpret_cast<int32_t *>(lsg + DC * cpr * 32);   // [nd][totL] leading
   int32_t *ibins = tab + DC * totL;                        // [nd][Jt] int32 (or FP32)
   float *fbins = reinterpret_cast<float *>(ibins);
   if (threadIdx.x == 0) {
@@ -224,7 +228,9 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
   const bool act0 = i0 < a.L, act1 = i0 + 128 < a.L;
   // last-mode tables in shared memory, one 16-byte word per (sketch, chunk,
   // lane): eight 16-bit entries (offset in bits 0..14, sign in bit 15) for
-  // the lane's elements e = 0..7, last-mode index i0 + (e / 4) * 128 + e % 4.
+  // the lane's elements e = 0..7, last-mode index i0 + (e / 4) * 128 + e % 4;
+  // the eight signs are also gathered into one mask word per (sketch, chunk,
+  // lane) in lsg.
   // Absent elements (past the end of the mode) get a distinct in-range
   // offset and value 0, so they add nothing and never collide.
   {
@@ -245,6 +251,13 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
       reinterpret_cast<uint16_t *>(ltab)[k] = uint16_t(t16);
     }
     if (bad) s_bad = 1;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nd * cpr * 32; k += NT) {
+    const uint16_t *t = reinterpret_cast<const uint16_t *>(ltab) + k * 8;
+    uint32_t m = 0;
+    for (int e = 0; e < 8; ++e) m |= uint32_t(t[e] >> 15) << e;
+    lsg[k] = m;
   }
 
   const int b = blockIdx.y;
@@ -302,28 +315,27 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
   const float carry = fx ? ldexpf(1.f, E + 7) : 0.f;     // 2^32 q
 
   // Fast scatter of one row into sketch d: eight int32 adds issued back to
-  // back, then one test for a wrap among them.  LNEG is the leading modes'
-  // sign, uniform across the warp.
-  auto scatter_fast = [&](auto lneg_c, int d, int base, const int *xi, const int *nxi) {
+  // back, then one test of their old values (bit 31 of old ^ 2 old is set
+  // iff |old| >= 2^30); only then are the adds checked for a wrap.  LNEG is
+  // the leading modes' sign, uniform across the warp.
+  auto scatter_fast = [&](auto lneg_c, int d, int base, const int *xi) {
     constexpr bool LNEG = decltype(lneg_c)::value;
     const uint4 tw = reinterpret_cast<const uint4 *>(ltab)[(d * cpr + c) * 32 + lane];
     const uint32_t w[4] = {tw.x, tw.y, tw.z, tw.w};
+    const uint32_t sg = lsg[(d * cpr + c) * 32 + lane];
     int32_t *bb = ibins + d * Jt + base;
     int val[8], old[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const uint32_t t = (e & 1) ? (w[e >> 1] >> 16) : w[e >> 1];
-      const bool sneg = ((t >> 15) & 1u) != 0;
-      val[e] = (sneg != LNEG) ? nxi[e] : xi[e];
+      const bool sneg = ((sg >> e) & 1u) != 0;
+      val[e] = (sneg != LNEG) ? -xi[e] : xi[e];
       old[e] = atomicAdd(bb + (t & 0x7fffu), val[e]);
     }
     int flag = 0;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int nw = int(unsigned(old[e]) + unsigned(val[e]));
-      flag |= (old[e] ^ nw) & (val[e] ^ nw);
-    }
-    if (flag < 0) {                                    // rare: carry out of a bin
+    for (int e = 0; e < 8; ++e) flag |= old[e] ^ (old[e] << 1);
+    if (flag < 0) {                                    // rare: a large bin
       float *od = outb + (d0 + d) * Jt + base;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
@@ -352,15 +364,14 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
       for (int n = 0; n < kMaxN; ++n) idx[n] = nidx[n];
       const float v[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
       if (row + rstride < a.rows) load(row_addr(row + rstride, nidx), n0, n1);
-      int xi[8], nxi[8];
+      int xi[8];
       float rv[8];
       unsigned fastm = 0;          // bit e: entry e goes through the integer path
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const float u = v[e] * inv_q;
-        const bool fast = fabsf(u) < 2147483520.f;       // 2^31 - 2^7; false for NaN
+        const bool fast = fabsf(u) < 1073741760.f;       // 2^30 - 2^6; false for NaN
         xi[e] = fast ? __float2int_rn(u) : 0;
-        nxi[e] = -xi[e];
         fastm |= unsigned(fast) << e;
         if (MODE == 0) {
           sumsq = fmaf(u, u, sumsq);       // in units of q^2
@@ -383,9 +394,9 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
             }
           }
           if (neg)
-            scatter_fast(std::true_type(), d, base, xi, nxi);
+            scatter_fast(std::true_type(), d, base, xi);
           else
-            scatter_fast(std::false_type(), d, base, xi, nxi);
+            scatter_fast(std::false_type(), d, base, xi);
         }
         continue;
       }
@@ -565,7 +576,7 @@ extern "C" int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
   int64_t totL = tot - host_I[N - 1];
   const int cpr_rows = int((host_I[N - 1] + 255) / 256);
   auto rows_smem = [&](int dc) {
-    return size_t(dc) * (size_t(totL) + size_t(Jt)) * 4 + size_t(dc) * size_t(cpr_rows) * 512;
+    return size_t(dc) * (size_t(totL) + size_t(Jt)) * 4 + size_t(dc) * size_t(cpr_rows) * 640;
   };
   int ngroups = 1;
   while (ngroups < D && rows_smem((D + ngroups - 1) / ngroups) > 200 * 1024) ++ngroups;
@@ -600,11 +611,11 @@ extern "C" int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
       return check_cuda(ctx, cudaGetLastError(), "dense_rows_kernel");
     };
     switch (N - 1) {
-      case 0: return launch_rows(dense_rows_kernel<512, 0>, 512);
-      case 1: return launch_rows(dense_rows_kernel<512, 1>, 512);
-      case 2: return launch_rows(dense_rows_kernel<512, 2>, 512);
-      case 3: return launch_rows(dense_rows_kernel<512, 3>, 512);
-      default: return launch_rows(dense_rows_kernel<512, -1>, 512);
+      case 0: return launch_rows(dense_rows_kernel<768, 0>, 768);
+      case 1: return launch_rows(dense_rows_kernel<768, 1>, 768);
+      case 2: return launch_rows(dense_rows_kernel<768, 2>, 768);
+      case 3: return launch_rows(dense_rows_kernel<768, 3>, 768);
+      default: return launch_rows(dense_rows_kernel<768, -1>, 768);
     }
   }
   if (vec)
