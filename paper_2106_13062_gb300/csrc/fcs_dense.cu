@@ -366,21 +366,33 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
       if (row + rstride < a.rows) load(row_addr(row + rstride, nidx), n0, n1);
       int xi[8];
       float rv[8];
-      unsigned fastm = 0;          // bit e: entry e goes through the integer path
+      // one sum of squares per row decides the fast path: below 2^60 every
+      // |u| < 2^30 and nothing is NaN or Inf
+      float srow = 0.f;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const float u = v[e] * inv_q;
-        const bool fast = fabsf(u) < 1073741760.f;       // 2^30 - 2^6; false for NaN
-        xi[e] = fast ? __float2int_rn(u) : 0;
-        fastm |= unsigned(fast) << e;
-        if (MODE == 0) {
-          sumsq = fmaf(u, u, sumsq);       // in units of q^2
-          nfx += unsigned(fast);
-        }
-        rv[e] = MODE == 1 ? (fast ? fmaf(-q, __int2float_rn(xi[e]), v[e]) : 0.f) : v[e];
+        xi[e] = __float2int_rn(u);
+        srow = fmaf(u, u, srow);
       }
       const bool fast_row =
-          MODE == 0 && tables_ok && __all_sync(0xffffffffu, fastm == 0xffu);
+          MODE == 0 && tables_ok && __all_sync(0xffffffffu, srow < 1.152921504606846976e18f);
+      unsigned fastm = 0xffu;      // bit e: entry e goes through the integer path
+      if (MODE == 0) {
+        sumsq += srow;             // in units of q^2
+        nfx += 8u;
+      }
+      if (!fast_row) {
+        fastm = 0u;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float u = v[e] * inv_q;
+          const bool fast = fabsf(u) < 1073741760.f;     // 2^30 - 2^6; false for NaN
+          if (!fast) xi[e] = 0;
+          fastm |= unsigned(fast) << e;
+          rv[e] = MODE == 1 ? (fast ? fmaf(-q, __int2float_rn(xi[e]), v[e]) : 0.f) : v[e];
+        }
+      }
       if (fast_row) {
 #pragma unroll 1
         for (int d = 0; d < nd; ++d) {
