@@ -23,7 +23,11 @@
  *    A larger ldh lets a call use a contiguous run of modes of a wider table
  *    (e.g. modes 3..4 of an order-4 table for the Kronecker workload).
  *  - Limits: 1 <= N <= 8, 1 <= D <= 16, 1 <= J_n, I_n >= 1, every entry of
- *    h for mode n in [0, J_n).  FFT-based calls (CP route, contractions,
+ *    h for mode n in [0, J_n).  A hash value outside that range never makes
+ *    a kernel touch memory out of bounds: the dense route drops the entries
+ *    that use it (for that sketch only); gathers (recovery, contractions)
+ *    return NaN when the summed bin leaves [0, Jt) and are otherwise
+ *    unspecified.  FFT-based calls (CP route, contractions,
  *    outer combine) need Jt <= 2^20: the FFT length is P = smallest power of
  *    two >= Jt, 16 <= P <= 2^20, else FCS_EUNSUPPORTED.  P <= 16384 runs one
  *    transform per CTA in shared memory; longer transforms use a two-pass
@@ -106,6 +110,10 @@ int fcs_make_hashes(fcs_ctx *ctx, uint64_t seed, int N, const int64_t *host_I,
 /*
  * fcs_sketch_dense -- FCS of a general tensor by the signed scatter of
  * eq. (FCS_asyn):  out_d[sum_n h_n(i_n)] += prod_n s_n(i_n) T(i_1..i_N).
+ *   With a contiguous last mode the per-CTA partial sums are exact int32
+ *   fixed-point sums (power-of-two step per CTA, wraps carried, outliers and
+ *   NaN/Inf added in FP32); the result is within FP32 rounding of the exact
+ *   sketch.
  *   host_I[N]: mode sizes; host_stride[N]: element strides of T (NULL = C
  *   order, last mode contiguous); T: FP32 tensor; out [D][Jt] FP32 (zeroed
  *   by the call, then accumulated).  nbatch tensors of the same shape may be

@@ -65,8 +65,10 @@ __global__ void __launch_bounds__(1024) dense_kernel(DenseArgs a) {
   auto entry = [&](int d, int64_t e) -> int32_t {
     return SMEM ? tab[d * tot + e] : packed_entry(a, d, int(e));
   };
+  // a hash value outside [0, J_n) in any mode drops the entry for sketch d
+  auto valid = [&](int32_t t, int n) { return unsigned(t >> 1) < unsigned(a.m.J[n]); };
   auto add = [&](int d, int64_t bin, float v) {
-    if (bin < 0 || bin >= Jt) return;     // hash value outside [0, J_n): skip
+    if (bin < 0 || bin >= Jt) return;
     if (SMEM)
       atomicAdd(&bins[d * Jt + bin], v);
     else
@@ -95,17 +97,19 @@ __global__ void __launch_bounds__(1024) dense_kernel(DenseArgs a) {
       const float vv[4] = {v.x, v.y, v.z, v.w};
       for (int d = 0; d < D; ++d) {
         int base = 0, neg = 0;
+        bool ok = true;
         for (int n = 0; n < N - 1; ++n) {
           const int32_t t = entry(d, a.m.off[n] + idx[n]);
           base += t >> 1;
           neg ^= t & 1;
+          ok = ok && valid(t, n);
         }
-        if (active) {
+        if (active && ok) {
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const int32_t t = entry(d, a.m.off[N - 1] + il + k);
             const float x = ((neg ^ t) & 1) ? -vv[k] : vv[k];
-            add(d, base + (t >> 1), x);
+            if (valid(t, N - 1)) add(d, base + (t >> 1), x);
           }
         }
       }
@@ -124,12 +128,14 @@ __global__ void __launch_bounds__(1024) dense_kernel(DenseArgs a) {
         const float x = Tb[addr];
         for (int d = 0; d < D; ++d) {
           int bin = 0, neg = 0;
+          bool ok = true;
           for (int n = 0; n < N; ++n) {
             const int32_t t = entry(d, a.m.off[n] + idx[n]);
             bin += t >> 1;
             neg ^= t & 1;
+            ok = ok && valid(t, n);
           }
-          add(d, bin, neg ? -x : x);
+          if (ok) add(d, bin, neg ? -x : x);
         }
       }
     }

@@ -121,3 +121,37 @@ def test_repeat_calls_bitwise_stable_bins(fcs, ctx, orc):
     ref = orc.fcs_dense(T.astype(np.float64), J, ho, so)
     assert_sketch_close(a, ref)
     assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("strided", [False, True])
+def test_invalid_hash_values_are_skipped(fcs, ctx, orc, strided):
+    """Hash values outside [0, J_n) (in a leading mode and in the last mode)
+    drop exactly the entries that use them, sketch by sketch; the rest
+    matches the definition.  strided=True goes through the general-stride
+    kernel."""
+    T = synth.gaussian(43, SHAPE)
+    D = 3
+    ho, so = orc.make_hashes(44, list(SHAPE), J, D)
+    bad = ho.copy()
+    off = [0, SHAPE[0], SHAPE[0] + SHAPE[1]]
+    bad[0, off[0] + 7] = J[0] + 5          # sketch 0, mode 0, index 7
+    bad[1, off[2] + 100] = -3              # sketch 1, last mode, index 100
+    bad[2, off[1] + 0] = 1 << 20           # sketch 2, mode 1, index 0
+    ref = np.empty((D, sum(J) - 2))
+    for d in range(D):
+        Td = T.copy()
+        hd = ho.copy()
+        for n in range(3):
+            sl = slice(off[n], off[n] + SHAPE[n])
+            for i in np.nonzero((bad[d, sl] < 0) | (bad[d, sl] >= J[n]))[0]:
+                idx = [slice(None)] * 3
+                idx[n] = i
+                Td[tuple(idx)] = 0.0
+        ref[d] = orc.fcs_dense(Td.astype(np.float64), J, hd, so)[d]
+    if strided:
+        base = cuda(np.ascontiguousarray(T.transpose(2, 0, 1)))
+        Tg = base.permute(1, 2, 0)
+    else:
+        Tg = cuda(T)
+    got = host(fcs.fcs_sketch_dense(ctx, Tg, J, cuda(bad), cuda(so)))
+    assert_sketch_close(got, ref)
