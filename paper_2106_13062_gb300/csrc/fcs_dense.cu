@@ -152,11 +152,11 @@ __global__ void __launch_bounds__(1024) dense_kernel(DenseArgs a) {
 // Row-chunk kernel (contiguous last mode, J_{N-1} < 2^15): warp w owns a
 // fixed chunk of 256 consecutive last-mode indices (two float4 per lane) and
 // walks the rows i_1..i_{N-1} of its batch item.  Because the chunk never
-// changes, the lane's last-mode bin offsets (16-bit pairs) and signs (one bit
-// each) for all D sketches stay in registers for the whole kernel; the
-// leading modes' partial hash and sign are the same for the whole warp, read
-// from shared memory once per row and sketch.  The next row's values are
-// prefetched while the current row is scattered.
+// changes, the lane's eight last-mode bin offsets (16-bit) and signs (one
+// mask word) per sketch are read from shared memory as two words per row and
+// sketch; the leading modes' partial hash and sign are the same for the whole
+// warp, read once per row and sketch.  The next row's values are prefetched
+// while the current row is scattered.
 //
 // Accumulation is exact integer fixed point: shared-memory FP32 atomics are a
 // compare-and-swap loop (about 6x slower than a 32-bit integer atomic add), so
