@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
         const int32_t t = packed_entry(a, d0 + d, int(offl + i));
         const uint32_t hv = uint32_t(t >> 1);
         bad |= int(hv >= JL);
-        t16 = (hv < JL ? hv : 0u) | (uint32_t(t & 1) << 15);
+        t16 = (hv < JL ? hv : 0u) | (uint32_t(t & 1) << 15);   // sign kept for lsg
       }
       reinterpret_cast<uint16_t *>(ltab)[k] = uint16_t(t16);
     }
@@ -265,6 +265,9 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
     for (int e = 0; e < 8; ++e) m |= uint32_t(t[e] >> 15) << e;
     lsg[k] = m;
   }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nd * cpr * 32 * 8; k += NT)
+    reinterpret_cast<uint16_t *>(ltab)[k] &= uint16_t(0x7fff);
 
   const int b = blockIdx.y;
   const float *Tb = a.T + b * a.tbs;
@@ -281,6 +284,36 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
         idx[n] = int(rr - q * In);
         rr = q;
         addr += idx[n] * a.stride[n];
+      }
+    }
+    return addr;
+  };
+  // rows advance by rstride: its mixed-radix digits over the leading modes
+  // let the next row's indices follow by digit-wise addition with carries
+  int rsd[kMaxN];
+  {
+    uint32_t rr = uint32_t(warps_used / cpr);
+#pragma unroll
+    for (int n = NLMAX - 1; n >= 0; --n) {
+      rsd[n] = 0;
+      if (leading(n)) {
+        const uint32_t In = uint32_t(a.m.I[n]);
+        rsd[n] = int(rr % In);
+        rr /= In;
+      }
+    }
+  }
+  auto next_row = [&](const int *idx, int *nidx) {
+    int carry = 0;
+    int64_t addr = 0;
+#pragma unroll
+    for (int n = NLMAX - 1; n >= 0; --n) {
+      if (leading(n)) {
+        const int In = int(a.m.I[n]);
+        const int v = idx[n] + rsd[n] + carry;
+        carry = v >= In;
+        nidx[n] = carry ? v - In : v;
+        addr += nidx[n] * a.stride[n];
       }
     }
     return addr;
@@ -324,31 +357,38 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
   // back, then one test of their old values (bit 31 of old ^ 2 old is set
   // iff |old| >= 2^30); only then are the adds checked for a wrap.  LNEG is
   // the leading modes' sign, uniform across the warp.
-  auto scatter_fast = [&](auto lneg_c, int d, int base, const int *xi) {
+  // per-sketch table and bin pointers of this lane, stepped once per sketch
+  const uint4 *ltab_l = reinterpret_cast<const uint4 *>(ltab) + c * 32 + lane;
+  const uint32_t *lsg_l = lsg + c * 32 + lane;
+  const int lstep = cpr * 32;
+  auto scatter_fast = [&](auto lneg_c, int d, int base, const int *xi, const uint4 *tp,
+                          const uint32_t *sp, int32_t *bins_d) {
     constexpr bool LNEG = decltype(lneg_c)::value;
-    const uint4 tw = reinterpret_cast<const uint4 *>(ltab)[(d * cpr + c) * 32 + lane];
+    const uint4 tw = *tp;
     const uint32_t w[4] = {tw.x, tw.y, tw.z, tw.w};
-    const uint32_t sg = lsg[(d * cpr + c) * 32 + lane];
-    int32_t *bb = ibins + d * Jt + base;
+    const uint32_t sg = *sp;
+    int32_t *bb = bins_d + base;
     int val[8], old[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const uint32_t t = (e & 1) ? (w[e >> 1] >> 16) : w[e >> 1];
+      const uint32_t off = (e & 1) ? (w[e >> 1] >> 16) : (w[e >> 1] & 0xffffu);
       const bool sneg = ((sg >> e) & 1u) != 0;
       val[e] = (sneg != LNEG) ? -xi[e] : xi[e];
-      old[e] = atomicAdd(bb + (t & 0x7fffu), val[e]);
+      old[e] = atomicAdd(bb + off, val[e]);
     }
+    // bit 31 of old + 2^30 is set iff |old| >= 2^30
     int flag = 0;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) flag |= old[e] ^ (old[e] << 1);
+    for (int e = 0; e < 8; e += 2)
+      flag |= int(unsigned(old[e]) + 0x40000000u) | int(unsigned(old[e + 1]) + 0x40000000u);
     if (flag < 0) {                                    // rare: a large bin
       float *od = outb + (d0 + d) * Jt + base;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const uint32_t t = (e & 1) ? (w[e >> 1] >> 16) : w[e >> 1];
+        const uint32_t off = (e & 1) ? (w[e >> 1] >> 16) : (w[e >> 1] & 0xffffu);
         const int nw = int(unsigned(old[e]) + unsigned(val[e]));
         if (((old[e] ^ nw) & (val[e] ^ nw)) < 0)
-          atomicAdd(od + (t & 0x7fffu), val[e] > 0 ? carry : -carry);
+          atomicAdd(od + off, val[e] > 0 ? carry : -carry);
       }
     }
   };
@@ -369,7 +409,7 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
 #pragma unroll
       for (int n = 0; n < kMaxN; ++n) idx[n] = nidx[n];
       const float v[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
-      if (row + rstride < a.rows) load(row_addr(row + rstride, nidx), n0, n1);
+      if (row + rstride < a.rows) load(next_row(idx, nidx), n0, n1);
       int xi[8];
       float rv[8];
       // one sum of squares per row decides the fast path: below 2^60 every
@@ -400,21 +440,32 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
         }
       }
       if (fast_row) {
+        const int32_t *tabn[kMaxN];
+#pragma unroll
+        for (int n = 0; n < NLMAX; ++n)
+          if (leading(n)) tabn[n] = tab + int(a.m.off[n] + idx[n]);
+        const uint4 *tp = ltab_l;
+        const uint32_t *sp = lsg_l;
+        int32_t *bins_d = ibins;
 #pragma unroll 1
         for (int d = 0; d < nd; ++d) {
           int base = 0, neg = 0;
 #pragma unroll
           for (int n = 0; n < NLMAX; ++n) {
             if (leading(n)) {
-              const int32_t t = tab[d * totL + int(a.m.off[n] + idx[n])];
+              const int32_t t = *tabn[n];
+              tabn[n] += totL;
               base += t >> 1;
               neg ^= t & 1;
             }
           }
           if (neg)
-            scatter_fast(std::true_type(), d, base, xi);
+            scatter_fast(std::true_type(), d, base, xi, tp, sp, bins_d);
           else
-            scatter_fast(std::false_type(), d, base, xi);
+            scatter_fast(std::false_type(), d, base, xi, tp, sp, bins_d);
+          tp += lstep;
+          sp += lstep;
+          bins_d += Jt;
         }
         continue;
       }
