@@ -662,8 +662,10 @@ extern "C" int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
       int per_sm = 1;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem_rows);
       if (per_sm < 1) per_sm = 1;
+      // CTAs per (batch item, sketch group): one wave in total (a partial
+      // second wave would double the time of the CTAs in it)
       const int64_t slots = int64_t(nbatch) * ngroups;
-      int64_t per_item = (int64_t(ctx->sm_count) * per_sm + slots - 1) / slots;
+      int64_t per_item = (int64_t(ctx->sm_count) * per_sm) / slots;
       // no more warps than (rows x chunks) work units
       const int64_t need_warps = a.rows * cpr;
       const int64_t need = (need_warps * 32 + nt - 1) / nt;
