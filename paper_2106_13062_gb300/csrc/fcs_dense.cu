@@ -632,7 +632,7 @@ extern "C" int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sm);
     if (per_sm < 1) per_sm = 1;
     int64_t want = int64_t(ctx->sm_count) * per_sm;         // CTAs in flight
-    int64_t per_item = (want + nbatch - 1) / nbatch;
+    int64_t per_item = want / nbatch;   // one wave
     const int64_t need = (a.units * 32 + threads - 1) / threads;
     if (per_item > need) per_item = need;
     if (per_item < 1) per_item = 1;

@@ -262,7 +262,7 @@ int launch_recover(fcs_ctx *ctx, RecoverArgs &a, int64_t nbatch) {
         int per_sm = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 1024, sm2);
         if (per_sm < 1) per_sm = 1;
-        int64_t per_item = (int64_t(ctx->sm_count) * per_sm + nbatch - 1) / nbatch;
+        int64_t per_item = (int64_t(ctx->sm_count) * per_sm) / nbatch;   // one wave
         const int64_t need = (a.M + 4095) / 4096;
         if (per_item > need) per_item = need;
         if (per_item < 1) per_item = 1;
@@ -284,7 +284,7 @@ int launch_recover(fcs_ctx *ctx, RecoverArgs &a, int64_t nbatch) {
       int per_sm = 1;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, sm2);
       if (per_sm < 1) per_sm = 1;
-      int64_t per_item = (int64_t(ctx->sm_count) * per_sm + nbatch - 1) / nbatch;
+      int64_t per_item = (int64_t(ctx->sm_count) * per_sm) / nbatch;   // one wave
       const int64_t need = (a.M + 511) / 512;
       if (per_item > need) per_item = need;
       if (per_item < 1) per_item = 1;
@@ -304,7 +304,7 @@ int launch_recover(fcs_ctx *ctx, RecoverArgs &a, int64_t nbatch) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
   if (per_sm < 1) per_sm = 1;
   int64_t want = int64_t(ctx->sm_count) * per_sm;
-  int64_t per_item = (want + nbatch - 1) / nbatch;
+  int64_t per_item = want / nbatch;   // one wave
   const int64_t need = (a.M + 255) / 256;
   if (per_item > need) per_item = need;
   if (per_item < 1) per_item = 1;
