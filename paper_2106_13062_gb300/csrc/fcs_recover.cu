@@ -20,6 +20,7 @@ struct RecoverArgs {
   float *raw;
   int64_t M;
   int64_t sbs, ibs, obs;   // batch strides
+  int64_t nbatch;
   int tot;
 };
 
@@ -159,9 +160,7 @@ __global__ void __launch_bounds__(1024) recover_simd_kernel(RecoverArgs a) {
   const int Jt = int(a.m.Jt);
   float *sk = reinterpret_cast<float *>(smem);
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem + ((size_t(D) * Jt * 4 + 15) & ~size_t(15)));
-  const int64_t b = blockIdx.y;
-  const float *skg = a.sketch + b * a.sbs;
-  for (int e = threadIdx.x; e < D * Jt; e += blockDim.x) sk[e] = __ldg(skg + e);
+  // the tables are the same for every batch item: staged once
   for (int e = threadIdx.x; e < tot * W; e += blockDim.x) {
     const int i = e / W, w = e - i * W;
     uint32_t v = 0;
@@ -175,11 +174,9 @@ __global__ void __launch_bounds__(1024) recover_simd_kernel(RecoverArgs a) {
     }
     tab[e] = v;
   }
-  __syncthreads();
-  const int32_t *idx = a.idx + b * a.ibs;
-  float *out = a.out + b * a.obs;
+  const int32_t *idx = a.idx;
+  float *out = a.out;
   const uint32_t M = uint32_t(a.M);
-  const uint32_t stride = gridDim.x * blockDim.x;
   int off[kMaxN], In[kMaxN];
 #pragma unroll
   for (int n = 0; n < kMaxN; ++n) {
@@ -225,20 +222,38 @@ __global__ void __launch_bounds__(1024) recover_simd_kernel(RecoverArgs a) {
     }
     __stcs(out + q, median_net<D>(v));
   };
-  // four samples per iteration: all index loads are issued before any use
+  // CTA k takes the k-th equal share of the flattened (item, sample) range,
+  // so one wave of CTAs covers every item; the sketches of each item the
+  // share touches (at most a few) are staged in turn.
+  const int64_t S = a.nbatch * a.M;
+  const int64_t lo = S * blockIdx.x / gridDim.x, hi = S * (blockIdx.x + 1) / gridDim.x;
   constexpr int U = 4;
-  uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-  for (; q + (U - 1) * stride < M; q += U * stride) {
-    int iv[U][kMaxN];
+  const uint32_t stride = blockDim.x;
+  for (int64_t pos = lo; pos < hi;) {
+    const int64_t b = pos / a.M;
+    const int64_t end = min(hi, (b + 1) * a.M);
+    __syncthreads();                         // readers of the previous sketches are done
+    const float *skg = a.sketch + b * a.sbs;
+    for (int e = threadIdx.x; e < D * Jt; e += blockDim.x) sk[e] = __ldg(skg + e);
+    __syncthreads();
+    idx = a.idx + b * a.ibs;
+    out = a.out + b * a.obs;
+    const uint32_t q1 = uint32_t(end - b * a.M);
+    uint32_t q = uint32_t(pos - b * a.M) + threadIdx.x;
+    // four samples per iteration: all index loads are issued before any use
+    for (; q + (U - 1) * stride < q1; q += U * stride) {
+      int iv[U][kMaxN];
 #pragma unroll
-    for (int u = 0; u < U; ++u) load(q + u * stride, iv[u]);
+      for (int u = 0; u < U; ++u) load(q + u * stride, iv[u]);
 #pragma unroll
-    for (int u = 0; u < U; ++u) one(q + u * stride, iv[u]);
-  }
-  for (; q < M; q += stride) {
-    int iv[kMaxN];
-    load(q, iv);
-    one(q, iv);
+      for (int u = 0; u < U; ++u) one(q + u * stride, iv[u]);
+    }
+    for (; q < q1; q += stride) {
+      int iv[kMaxN];
+      load(q, iv);
+      one(q, iv);
+    }
+    pos = end;
   }
 }
 
@@ -262,11 +277,12 @@ int launch_recover(fcs_ctx *ctx, RecoverArgs &a, int64_t nbatch) {
         int per_sm = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 1024, sm2);
         if (per_sm < 1) per_sm = 1;
-        int64_t per_item = (int64_t(ctx->sm_count) * per_sm) / nbatch;   // one wave
-        const int64_t need = (a.M + 4095) / 4096;
-        if (per_item > need) per_item = need;
-        if (per_item < 1) per_item = 1;
-        kern<<<dim3(unsigned(per_item), unsigned(nbatch)), 1024, sm2, ctx->stream>>>(a);
+        // one wave of CTAs over all items' samples (a few thousand per CTA)
+        int64_t grid = int64_t(ctx->sm_count) * per_sm;
+        const int64_t need = (nbatch * a.M + 4095) / 4096;
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        kern<<<unsigned(grid), 1024, sm2, ctx->stream>>>(a);
         return check_cuda(ctx, cudaGetLastError(), "recover_simd_kernel");
       };
       if (a.raw) return idx4 ? pick(recover_simd_kernel<D, true, true>)
@@ -348,6 +364,7 @@ extern "C" int fcs_recover(fcs_ctx *ctx, int N, const int64_t *host_I, const int
   a.sbs = nbatch > 1 ? sketch_batch_stride : 0;
   a.ibs = nbatch > 1 ? idx_batch_stride : 0;
   a.obs = nbatch > 1 ? out_batch_stride : 0;
+  a.nbatch = nbatch;
   DeviceGuard g(ctx->device);
   switch (D) {
 #define FCS_REC_CASE(K) \
