@@ -66,6 +66,8 @@ __device__ __forceinline__ void cp_run(const Prob &a, int d, int64_t r0, int64_t
   const int sb = a.sb;
 
   fill_twiddles<LOG2M, NT>(tws, tw);
+  LastPassTw<LOG2M, NT> ltw;
+  ltw.load(tw);
   for (int e = tid; e < sb / 4; e += NT) reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int v = 0; v < NV; ++v) accS[v * NT + tid] = make_float2(0.f, 0.f);
@@ -122,7 +124,7 @@ __device__ __forceinline__ void cp_run(const Prob &a, int d, int64_t r0, int64_t
       for (int e = tid; e < sb / 4; e += NT)
         reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
       fft_middle_passes<LOG2M, NT, 1>(B, tws);
-      fft_last_pass_unpack<LOG2M, NT>(B, tw, X);
+      fft_last_pass_unpack<LOG2M, NT>(B, ltw, X);
 #pragma unroll
       for (int e = 0; e < EPS; ++e)
 #pragma unroll

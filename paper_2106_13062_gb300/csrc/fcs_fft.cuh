@@ -202,13 +202,49 @@ __device__ __forceinline__ void unpack2(float2 za, float2 zb, float2 w, float2 &
   xb = cconj(csub(e, t));
 }
 
+// The twiddles of the fused last pass depend only on the thread's slots, not
+// on the data: a kernel that runs many transforms loads them into registers
+// once (LastPassTw::load) instead of from the global table in every last pass.
+// Both twiddle sources give W_M^(u 2^b) (w0) and W_P^u (wP), P = 2M, for the
+// slot u = threadIdx.x + e NT (u != 0, a live slot).
+template <int L, int NT>
+struct LastPassTw {
+  using LPs = LastPass<L, NT>;
+  float2 c0[LPs::EPS][LPs::LRL];
+  float2 cP[LPs::EPS];
+  __device__ __forceinline__ void load(const float2 *__restrict__ tw) {
+#pragma unroll
+    for (int e = 0; e < LPs::EPS; ++e) {
+      const int u = threadIdx.x + e * NT;
+      const bool live = u != 0 && (LPs::SLOTS % NT == 0 || u < LPs::SLOTS);
+#pragma unroll
+      for (int b = 0; b < LPs::LRL; ++b)
+        c0[e][b] = live ? __ldg(&tw[(u << b) << (kLogTwN - L)]) : make_float2(1.f, 0.f);
+      cP[e] = live ? __ldg(&tw[u << (kLogTwN - L - 1)]) : make_float2(1.f, 0.f);
+    }
+  }
+  __device__ __forceinline__ float2 w0(int e, int b, int) const { return c0[e][b]; }
+  __device__ __forceinline__ float2 wP(int e, int) const { return cP[e]; }
+};
+
+// The global table read inside the last pass (no registers held across it).
+template <int L>
+struct LastPassTwGlobal {
+  const float2 *__restrict__ tw;
+  __device__ __forceinline__ float2 w0(int, int b, int u) const {
+    return __ldg(&tw[(u << b) << (kLogTwN - L)]);
+  }
+  __device__ __forceinline__ float2 wP(int, int u) const {
+    return __ldg(&tw[u << (kLogTwN - L - 1)]);
+  }
+};
+
 // Fused last pass + real unpack.  X[e][b][r] receives the half-spectrum value
 // at index q(e, b, r) = j_b + r NS with j_0 = u, j_1 = (u ? NS - u : NS / 2),
 // u = threadIdx.x + e NT (inactive slots leave zeros); q = 0 holds the packed
 // pair (X[0], X[M]).
-template <int L, int NT>
-__device__ __forceinline__ void fft_last_pass_unpack(const float2 *B,
-                                                     const float2 *__restrict__ tw,
+template <int L, int NT, class TW>
+__device__ __forceinline__ void fft_last_pass_unpack(const float2 *B, const TW &ltw,
                                                      float2 (*X)[2][LastPass<L, NT>::RL]) {
   using LPs = LastPass<L, NT>;
   constexpr int RL = LPs::RL, LRL = LPs::LRL, NS = LPs::NS;
@@ -244,7 +280,7 @@ __device__ __forceinline__ void fft_last_pass_unpack(const float2 *B,
       float2 wp0[LRL], wp1[LRL];
 #pragma unroll
       for (int b = 0; b < LRL; ++b) {
-        wp0[b] = __ldg(&tw[(u << b) << (kLogTwN - L)]);
+        wp0[b] = ltw.w0(e, b, u);
         // exp(-2 pi i 2^b / RL) = unit64(64 * 2^b / RL)
         wp1[b] = cmul(unit64((64 >> LRL) << b), cconj(wp0[b]));
       }
@@ -261,7 +297,7 @@ __device__ __forceinline__ void fft_last_pass_unpack(const float2 *B,
     Dft<RL>::run(z1);
     float2 x0[RL], x1[RL];
     if (u != 0) {
-      const float2 wP = __ldg(&tw[u << (kLogTwN - L - 1)]);       // W_P^u
+      const float2 wP = ltw.wP(e, u);                             // W_P^u
 #pragma unroll
       for (int r = 0; r < RL; ++r) {
         // q = u + r NS; W_P^q = W_P^u exp(-i pi r / RL); partner in z1[RL-1-r]
@@ -302,9 +338,9 @@ __device__ __forceinline__ int last_pass_index(int e, int b, int r) {
 // Forward real FFT of the compact real buffer A (sb floats, everything past
 // them zero) into slot registers X.  Starts and ends with a barrier; A is
 // cleared (float4 stores; sb a multiple of 4) once the first pass has read it.
-template <int L, int NT>
+template <int L, int NT, class TW>
 __device__ __forceinline__ void rfft_to_slots(float *A, int sb, float2 *B, const float2 *tws,
-                                              const float2 *__restrict__ tw,
+                                              const TW &ltw,
                                               float2 (*X)[2][LastPass<L, NT>::RL]) {
   __syncthreads();
   fft_first_pass<L, NT>(A, sb, B);
@@ -312,8 +348,17 @@ __device__ __forceinline__ void rfft_to_slots(float *A, int sb, float2 *B, const
   for (int e = threadIdx.x; e < sb / 4; e += NT)
     reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
   fft_middle_passes<L, NT, 1>(B, tws);
-  fft_last_pass_unpack<L, NT>(B, tw, X);
+  fft_last_pass_unpack<L, NT>(B, ltw, X);
   __syncthreads();
+}
+
+// Same, reading the last-pass twiddles from the global table (for kernels
+// whose register budget cannot keep them).
+template <int L, int NT>
+__device__ __forceinline__ void rfft_to_slots(float *A, int sb, float2 *B, const float2 *tws,
+                                              const float2 *__restrict__ tw,
+                                              float2 (*X)[2][LastPass<L, NT>::RL]) {
+  rfft_to_slots<L, NT>(A, sb, B, tws, LastPassTwGlobal<L>{tw}, X);
 }
 
 // Write slot values X (a half spectrum) into B as the conjugated packed
