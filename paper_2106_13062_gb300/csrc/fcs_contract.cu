@@ -147,9 +147,12 @@ __global__ void __launch_bounds__(NT) spectrum_kernel(const float *__restrict__ 
   float *A = reinterpret_cast<float *>(smem + Lay::kA);
   const float *xd = x + blockIdx.x * ld;
   fill_twiddles<LOG2M, NT>(tws, tw);
+  float2 *lps = reinterpret_cast<float2 *>(smem + Lay::kLp);
+  LastPassTwShared<LOG2M, NT>::fill(lps, tw);
+  const LastPassTwShared<LOG2M, NT> ltw{lps};
   for (int j = threadIdx.x; j < sb; j += NT) A[j] = j < len ? __ldg(xd + j) : 0.f;
   float2 X[EPS][2][RL];
-  rfft_to_slots<LOG2M, NT>(A, sb, B, tws, tw, X);
+  rfft_to_slots<LOG2M, NT>(A, sb, B, tws, ltw, X);
   float2 *sd = spec + blockIdx.x * int64_t(M + 1);
 #pragma unroll
   for (int e = 0; e < EPS; ++e) {
@@ -188,6 +191,9 @@ __global__ void __launch_bounds__(NT) contract_kernel(ContractArgs a,
   const int sb = a.sb;
   const float2 *sd = a.spec + d * int64_t(M + 1);
   fill_twiddles<LOG2M, NT>(tws, tw);
+  float2 *lps = reinterpret_cast<float2 *>(smem + Lay::kLp);
+  LastPassTwShared<LOG2M, NT>::fill(lps, tw);
+  const LastPassTwShared<LOG2M, NT> ltw{lps};
   for (int e = tid; e < sb / 4; e += NT)
     reinterpret_cast<float4 *>(A)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
 
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(NT) contract_kernel(ContractArgs a,
       const int hb = __ldg(hn + i);
       if (unsigned(hb) < unsigned(sb)) atomicAdd(A + hb, v);
     }
-    rfft_to_slots<LOG2M, NT>(A, sb, B, tws, tw, X);
+    rfft_to_slots<LOG2M, NT>(A, sb, B, tws, ltw, X);
 #pragma unroll
     for (int e = 0; e < EPS; ++e)
 #pragma unroll

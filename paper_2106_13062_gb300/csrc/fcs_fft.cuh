@@ -227,6 +227,32 @@ struct LastPassTw {
   __device__ __forceinline__ float2 wP(int e, int) const { return cP[e]; }
 };
 
+// The same twiddles parked in shared memory, [e][b or LRL for W_P][thread]:
+// each thread writes and reads only its own column (no barrier needed), so a
+// kernel short of registers still avoids global loads in every last pass.
+template <int L, int NT>
+struct LastPassTwShared {
+  using LPs = LastPass<L, NT>;
+  static constexpr int kLen = LPs::EPS * (LPs::LRL + 1) * NT;   // float2 entries
+  const float2 *s;
+  __device__ __forceinline__ static void fill(float2 *dst, const float2 *__restrict__ tw) {
+    LastPassTw<L, NT> t;
+    t.load(tw);
+#pragma unroll
+    for (int e = 0; e < LPs::EPS; ++e) {
+#pragma unroll
+      for (int b = 0; b < LPs::LRL; ++b) dst[(e * (LPs::LRL + 1) + b) * NT + threadIdx.x] = t.c0[e][b];
+      dst[(e * (LPs::LRL + 1) + LPs::LRL) * NT + threadIdx.x] = t.cP[e];
+    }
+  }
+  __device__ __forceinline__ float2 w0(int e, int b, int) const {
+    return s[(e * (LPs::LRL + 1) + b) * NT + threadIdx.x];
+  }
+  __device__ __forceinline__ float2 wP(int e, int) const {
+    return s[(e * (LPs::LRL + 1) + LPs::LRL) * NT + threadIdx.x];
+  }
+};
+
 // The global table read inside the last pass (no registers held across it).
 template <int L>
 struct LastPassTwGlobal {
@@ -398,13 +424,16 @@ __device__ __forceinline__ void slots_to_conj_packed(float2 *B,
 }
 
 // Shared-memory layout for kernels built on rfft_to_slots: B (padded FFT
-// buffer) | twiddle table | A (compact real input of sb floats).
+// buffer) | twiddle table | last-pass twiddles (LastPassTwShared) | A
+// (compact real input of sb floats).
 template <int L>
 struct FftSmem {
   static constexpr size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
   static constexpr size_t kB = 0;
   static constexpr size_t kTw = up16(sizeof(float2) * padded_len(1 << L));
-  static constexpr size_t kA = up16(kTw + sizeof(float2) * plan_twlen(L));
+  static constexpr size_t kLp = up16(kTw + sizeof(float2) * plan_twlen(L));
+  static constexpr size_t kA =
+      up16(kLp + sizeof(float2) * LastPassTwShared<L, fft_threads(L)>::kLen);
   static size_t bytes(int sb) { return kA + sizeof(float) * size_t(sb); }
 };
 

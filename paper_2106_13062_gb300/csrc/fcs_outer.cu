@@ -32,6 +32,9 @@ __global__ void __launch_bounds__(NT) outer_kernel(const float *__restrict__ fa,
   const int64_t bi = blockIdx.y;
   const int d = blockIdx.x;
   fill_twiddles<LOG2M, NT>(tws, tw);
+  float2 *lps = reinterpret_cast<float2 *>(smem + Lay::kLp);
+  LastPassTwShared<LOG2M, NT>::fill(lps, tw);
+  const LastPassTwShared<LOG2M, NT> ltw{lps};
   float2 acc[EPS][2][RL], p[EPS][2][RL], X[EPS][2][RL];
 #pragma unroll
   for (int e = 0; e < EPS; ++e)
@@ -45,7 +48,7 @@ __global__ void __launch_bounds__(NT) outer_kernel(const float *__restrict__ fa,
       const int64_t len = side == 0 ? La : Lb;
       const float *x = (side == 0 ? fa : fb) + slice * len;
       for (int j = tid; j < sb; j += NT) A[j] = j < len ? __ldg(x + j) : 0.f;
-      rfft_to_slots<LOG2M, NT>(A, sb, B, tws, tw, X);
+      rfft_to_slots<LOG2M, NT>(A, sb, B, tws, ltw, X);
 #pragma unroll
       for (int e = 0; e < EPS; ++e)
 #pragma unroll
