@@ -354,10 +354,10 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
   const float carry = fx ? ldexpf(1.f, E + 7) : 0.f;     // 2^32 q
 
   // Fast scatter of one row into sketch d: eight int32 adds issued back to
-  // back, then one test of their old values (bit 31 of old ^ 2 old is set
-  // iff |old| >= 2^30); only then are the adds checked for a wrap.  LNEG is
-  // the leading modes' sign, uniform across the warp.
-  // per-sketch table and bin pointers of this lane, stepped once per sketch
+  // back, then one test of their old values (bit 31 of old + 2^30 is set iff
+  // |old| >= 2^30); only then are the adds checked for a wrap.  LNEG is the
+  // leading modes' sign, uniform across the warp.  The lane's table and bin
+  // pointers for sketch d are passed in (stepped once per sketch).
   const uint4 *ltab_l = reinterpret_cast<const uint4 *>(ltab) + c * 32 + lane;
   const uint32_t *lsg_l = lsg + c * 32 + lane;
   const int lstep = cpr * 32;
