@@ -299,16 +299,16 @@ class DenseWorkload:
         return {"workload": self.name, "order": self.N, "I": self.I, "J": self.J,
                 "D": self.D, "vectors": self.B, "Jt": self.Jt, "fft_len": self.P,
                 "tensor": "symmetric rank 10, weights 10..1, noise sigma 0.01",
-                "spectrum_cache": "on (the second contraction of a step reuses the sketch "
-                                  "spectra the first one computed)",
+                "contractions": "fcs_contract_both: T(u,u,u) and T(I,u,u) from one set of "
+                                "transforms",
                 "seed": self.seed}
 
     def sketches_per_step(self):
         return self.D
 
     def launches_per_step(self):
-        # hashes, zero + dense, spectrum (once: cached), 2 x (contract, median)
-        return 1 + 2 + 1 + 2 * 2
+        # hashes, zero + dense, spectrum, fused contraction, 2 medians
+        return 1 + 2 + 1 + 1 + 2
 
     def bytes(self):
         """Dense kernel: the tensor read once, tables read once, sketches
@@ -323,8 +323,6 @@ class DenseWorkload:
         self.Tg = torch.from_numpy(T).to(dev)
         self.ug = torch.from_numpy(u).to(dev)
         self.fT = torch.empty((self.D, self.Jt), dtype=torch.float32, device=dev)
-        # as in an RTPM loop: contractions against one sketch share its spectra
-        fcs.fcs_cache_spectra(ctx, True)
         self.fcs, self.ctx, self.dev = fcs, ctx, dev
 
     def step(self, k, marks, T=None, u=None):
@@ -335,10 +333,9 @@ class DenseWorkload:
         marks("dense_kernel")
         fcs.fcs_sketch_dense(self.ctx, T, self.Js, h, s, out=self.fT)
         marks("contract")
-        a = fcs.fcs_contract(self.ctx, fcs.FCS_CONTRACT_ALL, self.fT, [u, u, u],
-                             self.Is, self.Js, h, s)
-        b = fcs.fcs_contract(self.ctx, fcs.FCS_CONTRACT_FREE, self.fT, [None, u, u],
-                             self.Is, self.Js, h, s, free_mode=0)
+        # T(u,u,u) and T(I,u,u) from one set of transforms
+        a, b = fcs.fcs_contract_both(self.ctx, self.fT, [u, u, u], self.Is, self.Js, h, s,
+                                     free_mode=0)
         marks(None)
         return a, b
 

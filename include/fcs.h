@@ -338,6 +338,27 @@ int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
                  float *out_median, float *out_raw);
 
 /*
+ * fcs_contract_both -- both contractions of Sec. 4.1 for one set of vectors,
+ * from one set of transforms: with p_d = F(FCS_d T) prod_{n != m}
+ * conj F(CS_n v_n), the FREE result is IFFT(p_d) gathered as in
+ * fcs_contract, and the ALL result is (1/P) Re sum_k conj(p_d[k])
+ * F(CS_m v_m)[k], equal to eq. (T_uvw) because conj(p_d) F(CS_m v_m) =
+ * conj(F(FCS_d T)) prod_n F(CS_n v_n).  N + 1 transforms per (item, sketch)
+ * instead of 2N (the RTPM step: T(I,u,u) for the power iteration and
+ * T(u,u,u) for the eigenvalue).
+ *  host_vecs[N]: all N vectors, [B][I_n] each (the one of mode m too).
+ *  out_all [B], out_free [B][I_m]: medians over the D sketches.
+ *  out_all_raw: NULL or [B][D]; out_free_raw: NULL or [B][D][I_m].
+ *  Other arguments and the workspace as for fcs_contract.  For FFT lengths
+ *  above 16384 the two contractions run one after the other.
+ */
+int fcs_contract_both(fcs_ctx *ctx, int free_mode, int N, const int64_t *host_I,
+                      const int32_t *host_J, int D, const float *fcsT, int64_t B,
+                      const float *const *host_vecs, const int32_t *h,
+                      const int8_t *s, int64_t ldh, float *out_all, float *out_free,
+                      float *out_all_raw, float *out_free_raw);
+
+/*
  * fcs_cache_spectra -- enable (1) or disable (0, the default; drops every
  * entry) the context's cache of sketch spectra for fcs_contract.  When on,
  * the D half spectra of fcsT that a contraction computes are kept in device

@@ -95,6 +95,10 @@ def lib() -> C.CDLL:
                                            i32p, C.c_int, vp, C.c_int64,
                                            C.POINTER(C.c_void_p), vp, vp,
                                            C.c_int64, vp, vp]),
+                "fcs_contract_both": (C.c_int, [vp, C.c_int, C.c_int, i64p, i32p,
+                                                C.c_int, vp, C.c_int64,
+                                                C.POINTER(C.c_void_p), vp, vp,
+                                                C.c_int64, vp, vp, vp, vp]),
                 "fcs_recover": (C.c_int, [vp, C.c_int, i64p, i32p, C.c_int, vp,
                                           vp, vp, C.c_int64, C.c_int64, vp, vp,
                                           vp, C.c_int64, C.c_int64, C.c_int64,
@@ -184,7 +188,7 @@ def exported_symbols():
     return ["fcs_version", "fcs_create", "fcs_destroy", "fcs_set_stream",
             "fcs_last_error", "fcs_workspace_bytes", "fcs_make_hashes",
             "fcs_sketch_dense", "fcs_sketch_cp", "fcs_sketch_cp_noalloc",
-            "fcs_contract", "fcs_cache_spectra", "fcs_forget",
+            "fcs_contract", "fcs_contract_both", "fcs_cache_spectra", "fcs_forget",
             "fcs_fold", "fcs_sketch_inner", "fcs_rtpm", "fcs_als",
             "fcs_recover", "fcs_sketch_outer", "fcs_sketch_outer_sum",
             "fcs_batch_plan_create", "fcs_batch_plan_launch",
@@ -436,6 +440,39 @@ def fcs_contract(ctx: Context, kind: int, fcsT: torch.Tensor, vecs, I, J, h, s,
         ctx.handle, kind, free_mode, N, _arr(C.c_int64, I), _arr(C.c_int32, J), D,
         _ptr(fcsT), B, ptrs, _ptr(h), _ptr(s), ldh, _ptr(med), _ptr(rawt)))
     return (med, rawt) if raw else med
+
+
+def fcs_contract_both(ctx: Context, fcsT: torch.Tensor, vecs, I, J, h, s,
+                      free_mode: int = 0, ldh: int = 0, raw: bool = False):
+    """T(v_1..v_N) and T(v_1, .., I (mode free_mode), .., v_N) from one set
+    of transforms.  vecs[n]: [B, I_n] FP32 for every n.  Returns
+    (all [B], free [B, I_m]) medians over the sketches and, with raw=True,
+    also the per-sketch values ([B, D], [B, D, I_m])."""
+    ctx._sync_stream()
+    _need(fcsT, torch.float32, "fcsT")
+    ldh = _tables(h, s, ldh)
+    N = len(J)
+    D = fcsT.shape[0]
+    ptrs = (C.c_void_p * N)()
+    B = None
+    for n in range(N):
+        v = vecs[n]
+        _need(v, torch.float32, f"vecs[{n}]")
+        B = v.shape[0] if B is None else B
+        if v.shape != (B, int(I[n])):
+            raise ValueError(f"vecs[{n}] must be [B, I_{n}]")
+        ptrs[n] = v.data_ptr()
+    dev = fcsT.device
+    Im = int(I[free_mode])
+    med_all = torch.empty((B,), dtype=torch.float32, device=dev)
+    med_free = torch.empty((B, Im), dtype=torch.float32, device=dev)
+    raw_all = torch.empty((B, D), dtype=torch.float32, device=dev) if raw else None
+    raw_free = torch.empty((B, D, Im), dtype=torch.float32, device=dev) if raw else None
+    ctx.check(lib().fcs_contract_both(
+        ctx.handle, free_mode, N, _arr(C.c_int64, I), _arr(C.c_int32, J), D, _ptr(fcsT), B,
+        ptrs, _ptr(h), _ptr(s), ldh, _ptr(med_all), _ptr(med_free), _ptr(raw_all),
+        _ptr(raw_free)))
+    return (med_all, med_free, raw_all, raw_free) if raw else (med_all, med_free)
 
 
 def fcs_recover(ctx: Context, sketch: torch.Tensor, I, J, h, s, idx: torch.Tensor,

@@ -125,6 +125,7 @@ struct ContractArgs {
   const int8_t *s;
   float2 *spec;           // [D][M+1]
   float *raw;             // [B][D] or [B][D][I_m]
+  float *raw_all;         // kBoth: the T(v_1..v_N) estimates [B][D]
   float *out;             // [B] or [B][I_m]
   int sb;                 // compact count-sketch buffer (floats, multiple of 4)
 };
@@ -171,6 +172,10 @@ __global__ void __launch_bounds__(NT) spectrum_kernel(const float *__restrict__ 
       }
   }
 }
+
+// Internal kind: both contractions of one vector set from one set of
+// transforms (fcs_contract_both).
+constexpr int kBoth = 2;
 
 template <int LOG2M, int NT>
 __global__ void __launch_bounds__(NT) contract_kernel(ContractArgs a,
@@ -264,6 +269,46 @@ __global__ void __launch_bounds__(NT) contract_kernel(ContractArgs a,
       a.raw[b * a.D + d] = t / float(2 * M);
     }
     return;
+  }
+
+  if (a.kind == kBoth) {
+    // p = F_T prod_{n != m} conj(F_n), so conj(p) F_m = conj(F_T) prod_n F_n:
+    // T(v_1..v_N) is the Parseval sum of Re(conj(p) F_m) over the free
+    // mode's transform, taken before p goes into the inverse transform
+    const int m = a.free_mode;
+    __syncthreads();
+    const int32_t *hn = a.h + d * a.m.ldh + a.m.off[m];
+    const int8_t *sn = a.s + d * a.m.ldh + a.m.off[m];
+    const float *vn = a.vec[m] + b * a.m.I[m];
+    for (int64_t i = tid; i < a.m.I[m]; i += NT) {
+      float v = __ldg(vn + i);
+      if (__ldg(sn + i) < 0) v = -v;
+      const int hb = __ldg(hn + i);
+      if (unsigned(hb) < unsigned(sb)) atomicAdd(A + hb, v);
+    }
+    rfft_to_slots<LOG2M, NT>(A, sb, B, tws, ltw, X);
+    float part = 0.f;
+#pragma unroll
+    for (int e = 0; e < EPS; ++e) {
+      if (LPs::SLOTS % NT != 0 && tid + e * NT >= LPs::SLOTS) continue;
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const bool packed = bb == 0 && r == 0 && tid + e * NT == 0;
+          const float dot = p[e][bb][r].x * X[e][bb][r].x + p[e][bb][r].y * X[e][bb][r].y;
+          part += packed ? dot : 2.f * dot;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      float t = 0.f;
+      for (int w = 0; w < NT / 32; ++w) t += red[w];
+      a.raw_all[b * a.D + d] = t / float(2 * M);
+    }
   }
 
   // FREE: inverse transform of the product, then gather at h_m(i)
@@ -391,23 +436,27 @@ extern "C" int fcs_forget(fcs_ctx *ctx, const void *ptr) {
   return FCS_OK;
 }
 
-extern "C" int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
-                            const int64_t *host_I, const int32_t *host_J, int D,
-                            const float *fcsT, int64_t B, const float *const *host_vecs,
-                            const int32_t *h, const int8_t *s, int64_t ldh,
-                            float *out_median, float *out_raw) {
+namespace {
+
+// fcs_contract (kind ALL or FREE) and fcs_contract_both (kind kBoth: the FREE
+// result in out_median / out_raw, the ALL result in out_all / out_all_raw).
+int contract_call(fcs_ctx *ctx, int kind, int free_mode, int N, const int64_t *host_I,
+                  const int32_t *host_J, int D, const float *fcsT, int64_t B,
+                  const float *const *host_vecs, const int32_t *h, const int8_t *s,
+                  int64_t ldh, float *out_median, float *out_raw, float *out_all,
+                  float *out_all_raw) {
   if (!ctx) return FCS_EINVAL;
   ctx->err.clear();
   ContractArgs a{};
   int rc = make_modes(ctx, N, host_I, host_J, ldh, &a.m);
   if (rc) return rc;
-  if (kind != FCS_CONTRACT_ALL && kind != FCS_CONTRACT_FREE)
+  if (kind != FCS_CONTRACT_ALL && kind != FCS_CONTRACT_FREE && kind != kBoth)
     return set_error(ctx, FCS_EINVAL, "unknown contraction kind %d", kind);
-  if (kind == FCS_CONTRACT_FREE && (free_mode < 0 || free_mode >= N))
+  if (kind != FCS_CONTRACT_ALL && (free_mode < 0 || free_mode >= N))
     return set_error(ctx, FCS_EINVAL, "free_mode=%d outside [0,%d)", free_mode, N);
   if (D < 1 || D > kMaxD) return set_error(ctx, FCS_EINVAL, "D=%d outside [1,%d]", D, kMaxD);
   if (B < 1 || B > 65535) return set_error(ctx, FCS_EINVAL, "B=%lld outside [1,65535]", (long long)B);
-  if (!fcsT || !host_vecs || !h || !s || !out_median)
+  if (!fcsT || !host_vecs || !h || !s || !out_median || (kind == kBoth && !out_all))
     return set_error(ctx, FCS_EINVAL, "NULL pointer argument");
   for (int n = 0; n < N; ++n) {
     if (kind == FCS_CONTRACT_FREE && n == free_mode) {
@@ -437,6 +486,7 @@ extern "C" int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
     a.sb = int((jmax + 3) / 4 * 4);
   }
   const int64_t width = kind == FCS_CONTRACT_ALL ? 1 : host_I[free_mode];
+  const bool both = kind == kBoth;
   DeviceGuard g(ctx->device);
   bool hit = false;
   fcs_spec_cache::Entry *ent = spec_cache_get(ctx, fcsT, a.m.Jt, D, log2m, &hit);
@@ -445,20 +495,24 @@ extern "C" int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
   const bool big = log2p > kMaxLog2P;
   const size_t sbytes =
       (ent || big) ? 0 : (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
-  const size_t rbytes = out_raw ? 0 : sizeof(float) * size_t(B) * D * size_t(width);
-  if (big && rbytes) {
-    rc = ensure_raw(ctx, rbytes);
+  const size_t rbytes =
+      out_raw ? 0 : (sizeof(float) * size_t(B) * D * size_t(width) + 255) & ~size_t(255);
+  const size_t abytes = (both && !out_all_raw) ? sizeof(float) * size_t(B) * D : 0;
+  if (big && rbytes + abytes) {
+    rc = ensure_raw(ctx, rbytes + abytes);
     if (rc) return rc;
   }
   void *ws = nullptr;
-  if (!big && sbytes + rbytes > 0) {
-    rc = ensure_workspace(ctx, sbytes + rbytes, &ws);
+  if (!big && sbytes + rbytes + abytes > 0) {
+    rc = ensure_workspace(ctx, sbytes + rbytes + abytes, &ws);
     if (rc) return rc;
   }
+  char *rbase = big ? reinterpret_cast<char *>(ctx->raw) : static_cast<char *>(ws) + sbytes;
   a.spec = ent ? ent->spec : static_cast<float2 *>(ws);
-  a.raw = out_raw ? out_raw
-                  : big ? ctx->raw
-                        : reinterpret_cast<float *>(static_cast<char *>(ws) + sbytes);
+  a.raw = out_raw ? out_raw : reinterpret_cast<float *>(rbase);
+  a.raw_all = !both ? nullptr
+              : out_all_raw ? out_all_raw
+                            : reinterpret_cast<float *>(rbase + rbytes);
   if (hit) {
     // the spectrum may have been written on another stream
     rc = check_cuda(ctx, cudaStreamWaitEvent(ctx->stream, ent->ready, 0), "cudaStreamWaitEvent");
@@ -466,8 +520,20 @@ extern "C" int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
   }
   rc = FCS_EUNSUPPORTED;
   if (log2p > kMaxLog2P) {
-    rc = big_contract(ctx, a.m, kind, free_mode, D, fcsT, B, a.vec, h, s, ent ? ent->spec : nullptr,
-                      !hit, ent ? ent->ready : nullptr, a.raw, log2p);
+    if (both) {
+      // the long-FFT route runs the two contractions one after the other
+      // (the second reuses the cached spectra when the cache is on)
+      rc = big_contract(ctx, a.m, FCS_CONTRACT_ALL, free_mode, D, fcsT, B, a.vec, h, s,
+                        ent ? ent->spec : nullptr, !hit, ent ? ent->ready : nullptr, a.raw_all,
+                        log2p);
+      if (!rc)
+        rc = big_contract(ctx, a.m, FCS_CONTRACT_FREE, free_mode, D, fcsT, B, a.vec, h, s,
+                          ent ? ent->spec : nullptr, ent == nullptr, nullptr, a.raw, log2p);
+    } else {
+      rc = big_contract(ctx, a.m, kind, free_mode, D, fcsT, B, a.vec, h, s,
+                        ent ? ent->spec : nullptr, !hit, ent ? ent->ready : nullptr, a.raw,
+                        log2p);
+    }
   } else {
     FCS_DISPATCH_LOG2M(log2m, rc = launch_contract<L>(ctx, a, a.m.Jt, !hit,
                                                       ent ? ent->ready : nullptr));
@@ -480,5 +546,34 @@ extern "C" int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
     rc = check_cuda(ctx, cudaEventRecord(ent->used, ctx->stream), "cudaEventRecord");
     if (rc) return rc;
   }
+  if (both) {
+    rc = launch_median(ctx, D, a.raw_all, B, 1, out_all);
+    if (rc) return rc;
+  }
   return launch_median(ctx, D, a.raw, B, width, out_median);
+}
+
+}  // namespace
+
+extern "C" int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
+                            const int64_t *host_I, const int32_t *host_J, int D,
+                            const float *fcsT, int64_t B, const float *const *host_vecs,
+                            const int32_t *h, const int8_t *s, int64_t ldh,
+                            float *out_median, float *out_raw) {
+  if (kind != FCS_CONTRACT_ALL && kind != FCS_CONTRACT_FREE) {
+    if (!ctx) return FCS_EINVAL;
+    ctx->err.clear();
+    return set_error(ctx, FCS_EINVAL, "unknown contraction kind %d", kind);
+  }
+  return contract_call(ctx, kind, free_mode, N, host_I, host_J, D, fcsT, B, host_vecs, h, s, ldh,
+                       out_median, out_raw, nullptr, nullptr);
+}
+
+extern "C" int fcs_contract_both(fcs_ctx *ctx, int free_mode, int N, const int64_t *host_I,
+                                 const int32_t *host_J, int D, const float *fcsT, int64_t B,
+                                 const float *const *host_vecs, const int32_t *h,
+                                 const int8_t *s, int64_t ldh, float *out_all, float *out_free,
+                                 float *out_all_raw, float *out_free_raw) {
+  return contract_call(ctx, kBoth, free_mode, N, host_I, host_J, D, fcsT, B, host_vecs, h, s,
+                       ldh, out_free, out_free_raw, out_all, out_all_raw);
 }
