@@ -513,12 +513,31 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
       }
     }
   };
-  auto flush_float = [&]() {
-    for (int64_t e = threadIdx.x; e < nd * Jt; e += NT) {
-      const float x = fbins[e];
-      if (x != 0.f) atomicAdd(&outb[d0 * Jt + e], x);
+  // Add the CTA's bins (value(e) for local bin e) to the output: 16-byte
+  // vector reductions over the aligned middle, scalar atomics at the ends.
+  auto flush = [&](auto value) {
+    float *dst = outb + d0 * Jt;
+    const int64_t n = nd * Jt;
+    int64_t head = int64_t((16 - (reinterpret_cast<uintptr_t>(dst) & 15)) & 15) / 4;
+    if (head > n) head = n;
+    const int64_t body = head + ((n - head) & ~int64_t(3));
+    for (int64_t e = threadIdx.x; e < head; e += NT) {
+      const float x = value(e);
+      if (x != 0.f) atomicAdd(dst + e, x);
+    }
+    for (int64_t e = head + 4 * int64_t(threadIdx.x); e < body; e += 4 * int64_t(NT)) {
+      const float x0 = value(e), x1 = value(e + 1), x2 = value(e + 2), x3 = value(e + 3);
+      if (x0 != 0.f || x1 != 0.f || x2 != 0.f || x3 != 0.f)
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + e), "f"(x0),
+                     "f"(x1), "f"(x2), "f"(x3)
+                     : "memory");
+    }
+    for (int64_t e = body + threadIdx.x; e < n; e += NT) {
+      const float x = value(e);
+      if (x != 0.f) atomicAdd(dst + e, x);
     }
   };
+  auto flush_float = [&]() { flush([&](int64_t e) { return fbins[e]; }); };
 
   if (!fx) {                          // this CTA accumulates in FP32
     run_rows(std::integral_constant<int, 2>());
@@ -538,10 +557,7 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
     atomicAdd(&s_nfx, (unsigned long long)nfx);
   }
   __syncthreads();
-  for (int64_t e = threadIdx.x; e < nd * Jt; e += NT) {
-    const int32_t x = ibins[e];
-    if (x != 0) atomicAdd(&outb[d0 * Jt + e], __int2float_rn(x) * q);
-  }
+  flush([&](int64_t e) { return __int2float_rn(ibins[e]) * q; });
   // expected squared rounding error n q^2 / 12 against (1e-7 ||x||)^2, in
   // units of q^2 (the test is uniform across the CTA)
   if (!(float(s_nfx) * (1.f / 12.f) > 1e-14f * s_sumsq)) return;
