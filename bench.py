@@ -589,12 +589,34 @@ class BatchWorkload:
         self.fcs, self.ctx, self.dev = fcs, ctx, dev
         self.items = []
         probs = []
+        # every problem's factors and weights are views of one device buffer,
+        # and every output of another, so the end-to-end step moves each way
+        # in one transfer (segments padded to 16 bytes)
+        data = []
         for k, (I, J, R, D) in enumerate(self.shapes):
             U, lam = synth.cp_factors(self.seed * 1000 + k, I, R)
-            Ug = [torch.from_numpy(u).to(dev) for u in U]
-            lamg = torch.from_numpy(lam).to(dev)
+            data.append((U, lam))
+        pad4 = lambda n: (n + 3) // 4 * 4  # noqa: E731
+        n_in = sum(pad4(u.size) for U, lam in data for u in U) + \
+            sum(pad4(lam.size) for U, lam in data)
+        n_out = sum(pad4(D * jt_of(J)) for I, J, R, D in self.shapes)
+        self.inbuf = torch.empty(n_in, dtype=torch.float32, device=dev)
+        self.outbuf = torch.zeros(n_out, dtype=torch.float32, device=dev)
+        pos_in = pos_out = 0
+        for k, ((I, J, R, D), (U, lam)) in enumerate(zip(self.shapes, data)):
+            Ug = []
+            for u in U:
+                v = self.inbuf[pos_in:pos_in + u.size].view(u.shape)
+                v.copy_(torch.from_numpy(u))
+                Ug.append(v)
+                pos_in += pad4(u.size)
+            lamg = self.inbuf[pos_in:pos_in + lam.size]
+            lamg.copy_(torch.from_numpy(lam))
+            pos_in += pad4(lam.size)
+            out = self.outbuf[pos_out:pos_out + D * jt_of(J)].view(D, jt_of(J))
+            pos_out += pad4(D * jt_of(J))
             h, s = fcs.fcs_make_hashes(ctx, k, I, J, D)
-            pr, out = fcs.cp_problem(Ug, lamg, J, h, s)
+            pr, out = fcs.cp_problem(Ug, lamg, J, h, s, out=out)
             probs.append(pr)
             self.items.append((Ug, lamg, h, s, out, J))
         self.grain = fcs.fcs_batch_autotune(ctx, probs)
@@ -621,18 +643,14 @@ class BatchWorkload:
 
     def e2e_prepare(self):
         import torch
-        self.outh = [torch.empty(it[4].shape, dtype=torch.float32).pin_memory() for it in self.items]
-        self.Uh = [[u.cpu().pin_memory() for u in it[0]] for it in self.items]
-        return (sum(u.numel() * 4 for us in self.Uh for u in us),
-                sum(o.numel() * 4 for o in self.outh))
+        self.inh = self.inbuf.cpu().pin_memory()
+        self.outh = torch.empty(self.outbuf.shape, dtype=torch.float32).pin_memory()
+        return self.inh.numel() * 4, self.outh.numel() * 4
 
     def e2e_step(self, k):
-        for it, us in zip(self.items, self.Uh):
-            for dst, src in zip(it[0], us):
-                dst.copy_(src, non_blocking=True)
+        self.inbuf.copy_(self.inh, non_blocking=True)
         self.graph.replay()
-        for it, oh in zip(self.items, self.outh):
-            oh.copy_(it[4], non_blocking=True)
+        self.outh.copy_(self.outbuf, non_blocking=True)
 
     def check(self):
         import torch
