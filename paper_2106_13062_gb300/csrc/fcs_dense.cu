@@ -30,6 +30,10 @@ struct DenseArgs {
   int64_t cpr;          // chunks per row (vector path) / entries per warp unit
   int64_t units;        // work units per batch item
   int tot;              // sum I_n
+  // row-chunk kernel: offset of leading mode n in the staged compact table
+  // (the modes may be permuted so that a unit-stride mode comes last; the
+  // table entry of mode n, index i stays at h[d*ldh + m.off[n] + i])
+  int64_t coff[kMaxN];
 };
 
 __global__ void zero_out_kernel(float *out, int64_t len, int64_t obs) {
@@ -214,11 +218,11 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
     for (int e = threadIdx.x; e < nd * totL; e += NT) {
       const int d = e / totL;
       const int k = e - d * totL;
-      const int32_t t = packed_entry(a, d0 + d, k);
       int n = 0;
 #pragma unroll
       for (int m = 1; m < kMaxN - 1; ++m)
-        if (m < N - 1 && k >= a.m.off[m]) n = m;
+        if (m < N - 1 && k >= a.coff[m]) n = m;
+      const int32_t t = packed_entry(a, d0 + d, int(a.m.off[n] + (k - a.coff[n])));
       bad |= int(unsigned(t >> 1) >= unsigned(a.m.J[n]));
       tab[e] = t;
     }
@@ -443,7 +447,7 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
         const int32_t *tabn[kMaxN];
 #pragma unroll
         for (int n = 0; n < NLMAX; ++n)
-          if (leading(n)) tabn[n] = tab + int(a.m.off[n] + idx[n]);
+          if (leading(n)) tabn[n] = tab + int(a.coff[n] + idx[n]);
         const uint4 *tp = ltab_l;
         const uint32_t *sp = lsg_l;
         int32_t *bins_d = ibins;
@@ -478,7 +482,7 @@ __global__ void __launch_bounds__(NT) dense_rows_kernel(DenseArgs a, int totL, i
 #pragma unroll
         for (int n = 0; n < NLMAX; ++n) {
           if (leading(n)) {
-            const int32_t t = tab[d * totL + int(a.m.off[n] + idx[n])];
+            const int32_t t = tab[d * totL + int(a.coff[n] + idx[n])];
             base += t >> 1;
             neg ^= t & 1;
             row_ok = row_ok && unsigned(t >> 1) < unsigned(a.m.J[n]);
@@ -608,9 +612,39 @@ extern "C" int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
     a.stride[n] = host_stride ? host_stride[n] : st;
     st *= host_I[n];
   }
-  a.L = host_I[N - 1];
+  // FCS does not depend on the order of the modes (bin and sign are a sum and
+  // a product over them): when the last mode is not the contiguous one but
+  // another is, that mode is moved last so the row-chunk kernel applies.
+  // Only the per-mode geometry moves; the hash tables stay where they are.
+  if (a.stride[N - 1] != 1) {
+    int k = -1;
+    for (int n = N - 2; n >= 0 && k < 0; --n)
+      if (a.stride[n] == 1 && a.m.I[n] >= 4) k = n;
+    if (k >= 0) {
+      const int64_t Ik = a.m.I[k], ok = a.m.off[k], sk = a.stride[k];
+      const int32_t Jk = a.m.J[k];
+      for (int n = k; n < N - 1; ++n) {
+        a.m.I[n] = a.m.I[n + 1];
+        a.m.J[n] = a.m.J[n + 1];
+        a.m.off[n] = a.m.off[n + 1];
+        a.stride[n] = a.stride[n + 1];
+      }
+      a.m.I[N - 1] = Ik;
+      a.m.J[N - 1] = Jk;
+      a.m.off[N - 1] = ok;
+      a.stride[N - 1] = sk;
+    }
+  }
+  {
+    int64_t c = 0;
+    for (int n = 0; n < kMaxN; ++n) {
+      a.coff[n] = c;
+      if (n < N - 1) c += a.m.I[n];
+    }
+  }
+  a.L = a.m.I[N - 1];
   a.rows = 1;
-  for (int n = 0; n < N - 1; ++n) a.rows *= host_I[n];
+  for (int n = 0; n < N - 1; ++n) a.rows *= a.m.I[n];
 
   bool vec = a.stride[N - 1] == 1 && a.L % 4 == 0 &&
              (reinterpret_cast<uintptr_t>(T) & 15) == 0 && (a.tbs % 4) == 0;
@@ -658,8 +692,8 @@ extern "C" int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
   // row-chunk kernel: contiguous last mode, 15-bit last-mode offsets.  The D
   // sketches are split into the fewest groups (one per blockIdx.z) whose
   // bins and tables fit in shared memory; each group reads T once.
-  int64_t totL = tot - host_I[N - 1];
-  const int cpr_rows = int((host_I[N - 1] + 255) / 256);
+  int64_t totL = tot - a.m.I[N - 1];
+  const int cpr_rows = int((a.m.I[N - 1] + 255) / 256);
   auto rows_smem = [&](int dc) {
     return size_t(dc) * (size_t(totL) + size_t(Jt)) * 4 + size_t(dc) * size_t(cpr_rows) * 640;
   };
@@ -667,7 +701,7 @@ extern "C" int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
   while (ngroups < D && rows_smem((D + ngroups - 1) / ngroups) > 200 * 1024) ++ngroups;
   const int DC = (D + ngroups - 1) / ngroups;
   const size_t smem_rows = rows_smem(DC);
-  if (vec && host_J[N - 1] <= 32767 && smem_rows <= 200 * 1024 && a.rows < (int64_t(1) << 31)) {
+  if (vec && a.m.J[N - 1] <= 32767 && smem_rows <= 200 * 1024 && a.rows < (int64_t(1) << 31)) {
     const int cpr = cpr_rows;
     auto launch_rows = [&](auto kern, int nt) -> int {
       if (smem_rows > 48 * 1024) {

@@ -155,3 +155,19 @@ def test_invalid_hash_values_are_skipped(fcs, ctx, orc, strided):
         Tg = cuda(T)
     got = host(fcs.fcs_sketch_dense(ctx, Tg, J, cuda(bad), cuda(so)))
     assert_sketch_close(got, ref)
+
+
+@pytest.mark.parametrize("perm", [(2, 0, 1), (1, 2, 0), (0, 2, 1)])
+def test_contiguous_mode_moved_last(fcs, ctx, orc, perm):
+    """Views whose contiguous mode is not the last one: the modes are
+    reordered internally (FCS does not depend on their order) so the
+    integer-accumulating row kernel still runs; the sketch must equal the
+    definition for the view's own mode order."""
+    base = synth.gaussian(45, (48, 40, 64))
+    Tv = np.ascontiguousarray(base.transpose(perm))
+    I = list(Tv.shape)
+    Jv = [37, 53, 29]
+    ho, so = orc.make_hashes(46, I, Jv, 3)
+    ref = orc.fcs_dense(Tv.astype(np.float64), Jv, ho, so)
+    got = host(fcs.fcs_sketch_dense(ctx, cuda(base).permute(*perm), Jv, cuda(ho), cuda(so)))
+    assert_sketch_close(got, ref)
