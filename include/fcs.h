@@ -110,10 +110,11 @@ int fcs_make_hashes(fcs_ctx *ctx, uint64_t seed, int N, const int64_t *host_I,
 /*
  * fcs_sketch_dense -- FCS of a general tensor by the signed scatter of
  * eq. (FCS_asyn):  out_d[sum_n h_n(i_n)] += prod_n s_n(i_n) T(i_1..i_N).
- *   With a contiguous last mode the per-CTA partial sums are exact int32
- *   fixed-point sums (power-of-two step per CTA, wraps carried, outliers and
- *   NaN/Inf added in FP32); the result is within FP32 rounding of the exact
- *   sketch.
+ *   When one mode is contiguous (moved last internally if it is not the
+ *   last; the sketch does not depend on mode order), the per-CTA partial
+ *   sums are exact int32 fixed-point sums (power-of-two step per CTA, wraps
+ *   carried, outliers and NaN/Inf added in FP32); the result is within FP32
+ *   rounding of the exact sketch.  Other layouts accumulate in FP32.
  *   host_I[N]: mode sizes; host_stride[N]: element strides of T (NULL = C
  *   order, last mode contiguous); T: FP32 tensor; out [D][Jt] FP32 (zeroed
  *   by the call, then accumulated).  nbatch tensors of the same shape may be
