@@ -221,14 +221,24 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, int Ns, int log2NsR,
                                               const float2 *__restrict__ tw) {
   constexpr int NB = M / R;
   constexpr int PER = (NB + NT - 1) / NT;
+  constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+  static_assert((1 << LR) == R, "radix 2, 4, 8 or 16");
   float2 v[PER][R];
+  // W^(k 2^e), e < log2 R: loaded with the data, before the barrier; the
+  // other powers are products of at most log2 R of them
+  float2 wp[PER][LR];
   const int tid = threadIdx.x;
+  const int shift = kLogTwN - log2NsR;
 #pragma unroll
   for (int b = 0; b < PER; ++b) {
     const int j = tid + b * NT;
     if (NB % NT == 0 || j < NB) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[b][r] = buf[pad(j + r * NB)];
+      const int k = j & (Ns - 1);
+#pragma unroll
+      for (int e = 0; e < LR; ++e)
+        wp[b][e] = Ns > 1 ? __ldg(&tw[(k << e) << shift]) : make_float2(1.f, 0.f);
     }
   }
   __syncthreads();
@@ -238,10 +248,17 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, int Ns, int log2NsR,
     if (NB % NT == 0 || j < NB) {
       const int k = j & (Ns - 1);
       if (Ns > 1) {
-        const int shift = kLogTwN - log2NsR;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const float2 w = __ldg(&tw[(r * k) << shift]);
+          float2 w = make_float2(1.f, 0.f);
+          bool first = true;
+#pragma unroll
+          for (int e = 0; e < LR; ++e) {
+            if ((r >> e) & 1) {
+              w = first ? wp[b][e] : cmul(w, wp[b][e]);
+              first = false;
+            }
+          }
           v[b][r] = cmul(v[b][r], w);
         }
       }
