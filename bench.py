@@ -547,12 +547,12 @@ def mixed_cp_shapes(seed: int, count: int):
 
 
 def long_cp_launches(J) -> int:
-    """Kernels of one CP-route sketch with P > 16384 (two-pass FFT route):
-    Count Sketches, pass 1, [pass 2,] accumulate per chunk of transforms, then
-    pack, pass 1, [pass 2,] unpack for the inverse (one chunk here)."""
+    """Kernels of one CP-route sketch with P > 16384.  P = 32768: the one
+    fused kernel.  Longer (two-pass FFT route): Count Sketches, pass 1,
+    pass 2, accumulate per chunk of transforms, then pack, pass 1, pass 2,
+    unpack for the inverse (one chunk here)."""
     P = fft_len(jt_of(J))
-    p2 = 1 if P > 32768 else 0
-    return (3 + p2) + (3 + p2)
+    return 1 if P == 32768 else 8
 
 
 class BatchWorkload:

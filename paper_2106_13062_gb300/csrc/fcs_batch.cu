@@ -557,7 +557,7 @@ int plan_create(fcs_ctx *ctx, int nprob_all, const fcs_cp_problem *q_all, int gr
       Modes m{};
       make_modes(ctx, p.N, p.I, p.J, p.ldh, &m);
       const int log2p = ilog2_ceil(m.Jt);
-      need = std::max(need, big_sketch_cp_bytes(m, p.R, p.D, log2p, cap));
+      need = std::max(need, big_sketch_cp_bytes(m, p.R, p.D, log2p, cap, ctx->sm_count));
     }
     cudaError_t e = need > cap ? cudaErrorMemoryAllocation : cudaMalloc(&plan->long_ws, need);
     if (e != cudaSuccess) {

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(kNT1) pass1_kernel(Pass1Args a, const float2 *
   const int64_t M1 = int64_t(1) << a.L1;
   const int64_t len = a.lens[t % a.nlens];
   const float *x = a.src + t * a.src_ld;
+#pragma unroll
   for (int m2 = threadIdx.x; m2 < kM2; m2 += kNT1) {
     const int64_t m = m1 + M1 * m2;
     const float re = 2 * m < len ? __ldg(x + 2 * m) : 0.f;
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(kNT1) pass1_kernel(Pass1Args a, const float2 *
   __syncthreads();
   block_fft<kL2, kNT1>(B, tw);
   float2 *y = a.dst + t * (M1 << kL2) + int64_t(m1) * kM2;
+#pragma unroll
   for (int q = threadIdx.x; q < kM2; q += kNT1) y[q] = B[pad(q)];
 }
 
@@ -337,6 +339,124 @@ __global__ void unpack_real_kernel(const float2 *__restrict__ Z, int64_t M, floa
   }
 }
 
+// ---------------------------------------------------------------- P = 2^15
+// The CP route for P = 2^15 (M = 2^14: one block FFT per transform) in one
+// kernel, with nothing but the running products leaving the SM.  An item is
+// (sketch d, rank group g); a CTA takes items blockIdx.x, + gridDim.x, ...
+// For every rank r of its group and every mode n it scatters the Count
+// Sketch of column r of U_n (times lambda_r on mode 0) into shared memory,
+// transforms it, and multiplies the half spectrum into the running product
+// of rank r, which lives in the CTA's own slice of `prod` (pair q holds
+// slots A and B, the unpack_pair convention); after the last mode the
+// product is added to G_d with atomics.  The CTA that completes the last
+// group of sketch d (ticket counter) runs the inverse real FFT of G_d and
+// writes FCS_d.  Nothing waits on another CTA.
+struct Cp15Args {
+  Modes m;
+  int64_t R;
+  int D;
+  int groups;                 // rank groups per sketch
+  const float *U[kMaxN];
+  int64_t ldU[kMaxN];
+  const float *lambda;
+  const int32_t *h;
+  const int8_t *s;
+  float2 *G;                  // [D][M + 1] half spectra, zero at start
+  unsigned *ticket;           // [D], zero at start; the last group resets it
+  float4 *prod;               // [gridDim.x][M / 2] running products
+  float *out;                 // [D][Jt]
+};
+
+__global__ void __launch_bounds__(kNT1) cp15_kernel(Cp15Args a, const float2 *__restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int is_last;
+  constexpr int M = kM2, HALF = M / 2, PAIRS = HALF / kNT1;
+  float2 *B = reinterpret_cast<float2 *>(smem);
+  float *Bf = reinterpret_cast<float *>(smem);
+  float4 *B4 = reinterpret_cast<float4 *>(smem);
+  const int tid = threadIdx.x;
+  const int N = a.m.N;
+  float4 *prod = a.prod + int64_t(blockIdx.x) * HALF;
+  const int items = a.D * a.groups;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int d = item / a.groups, g = item - d * a.groups;
+    const int64_t r0 = a.R * g / a.groups, r1 = a.R * (g + 1) / a.groups;
+    float2 *Gd = a.G + int64_t(d) * (M + 1);
+    for (int64_t r = r0; r < r1; ++r) {
+      for (int n = 0; n < N; ++n) {
+        for (int i = tid; i < padded_len(M) / 2; i += kNT1) B4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        const int64_t In = a.m.I[n];
+        const int Jn = a.m.J[n];
+        const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
+        const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
+        const float *col = a.U[n] + r;
+        const int64_t ld = a.ldU[n];
+        const float w = (n == 0 && a.lambda) ? __ldg(a.lambda + r) : 1.f;
+        for (int64_t i = tid; i < In; i += kNT1) {
+          const int hb = __ldg(hn + i);
+          float v = __ldg(col + i * ld) * w;
+          if (__ldg(sn + i) < 0) v = -v;
+          if (unsigned(hb) < unsigned(Jn)) atomicAdd(Bf + real_off(hb), v);
+        }
+        __syncthreads();
+        block_fft<kL2, kNT1>(B, tw);
+        const bool last = n == N - 1;
+#pragma unroll
+        for (int e = 0; e < PAIRS; ++e) {
+          const int q = tid + e * kNT1;
+          float2 A, Bs;
+          unpack_pair<kL2>(B, q, tw, A, Bs);
+          if (n > 0) {
+            const float4 p = prod[q];
+            A = slot_mul(make_float2(p.x, p.y), A, q == 0);
+            Bs = cmul(make_float2(p.z, p.w), Bs);
+          }
+          if (!last) {
+            prod[q] = make_float4(A.x, A.y, Bs.x, Bs.y);
+          } else if (q == 0) {
+            atomicAdd(&Gd[0].x, A.x);
+            atomicAdd(&Gd[M].x, A.y);
+            atomicAdd(&Gd[HALF], Bs);
+          } else {
+            atomicAdd(&Gd[q], A);
+            atomicAdd(&Gd[M - q], Bs);
+          }
+        }
+        __syncthreads();              // B is cleared for the next transform
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(a.ticket + d, 1u) == unsigned(a.groups - 1);
+    __syncthreads();
+    if (!is_last) continue;
+    __threadfence();
+    // last group of sketch d: the inverse real FFT of G_d
+    for (int q = tid; q < HALF; q += kNT1) {
+      float2 Av, Bv;
+      if (q == 0) {
+        Av = make_float2(__ldcg(&Gd[0].x), __ldcg(&Gd[M].x));
+        Bv = __ldcg(&Gd[HALF]);
+      } else {
+        Av = __ldcg(&Gd[q]);
+        Bv = __ldcg(&Gd[M - q]);
+      }
+      pack_pair_conj<kL2>(B, q, Av, Bv, tw);
+    }
+    __syncthreads();
+    block_fft<kL2, kNT1>(B, tw);
+    const float sc = 1.0f / float(M);
+    float *od = a.out + int64_t(d) * a.m.Jt;
+    for (int64_t j = tid; j < a.m.Jt; j += kNT1) {
+      const float v = Bf[real_off(int(j))];
+      od[j] = (j & 1) ? -v * sc : v * sc;
+    }
+    if (tid == 0) a.ticket[d] = 0u;
+    __syncthreads();                  // B is reused by the next item
+  }
+}
+
 // ---------------------------------------------------------------- contractions
 // Half spectra of T transforms Z [T][M] into S [T][M+1] (bin 0 and M real).
 __global__ void half_spectrum_kernel(const float2 *__restrict__ Z, int64_t M,
@@ -504,7 +624,38 @@ void big_cp_plan(const Modes &m, int64_t R, int D, int log2p, size_t cap, int64_
 }
 }  // namespace
 
-size_t big_sketch_cp_bytes(const Modes &m, int64_t R, int D, int log2p, size_t cap) {
+namespace {
+// The fused route for P = 2^15 (cp15_kernel): rank groups per sketch, CTAs
+// (at most one per SM; each owns a running-product slice of M/2 float4) and
+// bytes under `cap`.  ctas = 0 when not even one slice fits.
+struct Cp15Plan {
+  int groups = 0;
+  int ctas = 0;
+  size_t gbytes = 0;          // G, then the tickets
+  size_t bytes = 0;
+};
+Cp15Plan cp15_plan(int64_t R, int D, int nsm, size_t cap) {
+  Cp15Plan p;
+  const size_t slice = sizeof(float4) * size_t(kM2 / 2);
+  p.gbytes = (sizeof(float2) * size_t(D) * size_t(kM2 + 1) + sizeof(unsigned) * size_t(D) + 255) &
+             ~size_t(255);
+  if (cap < p.gbytes + slice) return p;
+  nsm = std::max(nsm, 1);
+  const int64_t groups = std::max<int64_t>(1, std::min<int64_t>(R, nsm / D));
+  int64_t ctas = std::min<int64_t>(int64_t(D) * groups, nsm);
+  ctas = std::min<int64_t>(ctas, int64_t((cap - p.gbytes) / slice));
+  p.groups = int(groups);
+  p.ctas = int(ctas);
+  p.bytes = p.gbytes + slice * size_t(ctas);
+  return p;
+}
+}  // namespace
+
+size_t big_sketch_cp_bytes(const Modes &m, int64_t R, int D, int log2p, size_t cap, int nsm) {
+  if (log2p == kL2 + 1) {
+    const Cp15Plan f = cp15_plan(R, D, nsm, cap);
+    if (f.ctas > 0) return f.bytes;
+  }
   int64_t tc;
   size_t bytes;
   big_cp_plan(m, R, D, log2p, cap, &tc, &bytes);
@@ -519,10 +670,44 @@ int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *c
   const int N = m.N;
   const size_t gbytes = (sizeof(float2) * size_t(D) * size_t(M + 1) + 255) & ~size_t(255);
   const int64_t total = int64_t(D) * R * N;
+  const size_t cap = ext_ws ? ext_bytes : std::min(ctx->budget, kBigWorkspaceCap);
+  if (L1 == 0) {
+    const Cp15Plan f = cp15_plan(R, D, ctx->sm_count, cap);
+    if (f.ctas > 0) {
+      void *ws = ext_ws;
+      if (!ws) {
+        int rc = ensure_workspace(ctx, f.bytes, &ws);
+        if (rc) return rc;
+      }
+      Cp15Args a{};
+      a.m = m;
+      a.R = R;
+      a.D = D;
+      a.groups = f.groups;
+      for (int n = 0; n < N; ++n) {
+        a.U[n] = host_U[n];
+        a.ldU[n] = host_ldU[n];
+      }
+      a.lambda = lambda;
+      a.h = h;
+      a.s = s;
+      a.G = static_cast<float2 *>(ws);
+      a.ticket = reinterpret_cast<unsigned *>(a.G + size_t(D) * size_t(M + 1));
+      a.prod = reinterpret_cast<float4 *>(static_cast<char *>(ws) + f.gbytes);
+      a.out = out;
+      int rc = check_cuda(ctx, cudaMemsetAsync(ws, 0, f.gbytes, ctx->stream), "cudaMemsetAsync(G)");
+      if (rc) return rc;
+      const size_t smem = sizeof(float2) * padded_len(kM2);
+      cudaError_t e = cudaFuncSetAttribute(cp15_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(smem));
+      if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp15)");
+      cp15_kernel<<<unsigned(f.ctas), kNT1, smem, ctx->stream>>>(a, ctx->twiddle);
+      return check_cuda(ctx, cudaGetLastError(), "cp15_kernel");
+    }
+  }
   int64_t tc;
   size_t need;
-  big_cp_plan(m, R, D, log2p, ext_ws ? ext_bytes : std::min(ctx->budget, kBigWorkspaceCap),
-              &tc, &need);
+  big_cp_plan(m, R, D, log2p, cap, &tc, &need);
   void *ws = ext_ws;
   int rc = FCS_OK;
   if (ws) {

@@ -495,7 +495,7 @@ int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *c
                   const int8_t *s, float *out, int log2p, void *ext_ws = nullptr,
                   size_t ext_bytes = 0);
 // Device bytes big_sketch_cp uses when its buffer holds at most `cap` bytes.
-size_t big_sketch_cp_bytes(const Modes &m, int64_t R, int D, int log2p, size_t cap);
+size_t big_sketch_cp_bytes(const Modes &m, int64_t R, int D, int log2p, size_t cap, int nsm);
 int big_contract(fcs_ctx *ctx, const Modes &m, int kind, int free_mode, int D,
                  const float *fcsT, int64_t B, const float *const *vec, const int32_t *h,
                  const int8_t *s, float2 *spec, bool need_spec, cudaEvent_t spec_ready,

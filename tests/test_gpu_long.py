@@ -41,7 +41,9 @@ def _cp(fcs, ctx, orc, I, J, R, D, seed, budget_ctx=None):
 
 
 @pytest.mark.parametrize("I,J,R,D", [
-    ([200, 300, 250], [8192, 8192, 8192], 5, 3),      # Jt = 24574, P = 2^15 (pass 1 only)
+    ([200, 300, 250], [8192, 8192, 8192], 5, 3),      # Jt = 24574, P = 2^15 (fused kernel)
+    ([20000], [20000], 3, 2),                         # one mode: its transform is also the last
+    ([400, 300, 500, 200], [9000, 7000, 5000, 6000], 40, 10),   # 150 items of 2-3 ranks
     ([300, 400], [20000, 15000], 3, 2),               # Jt = 34999, P = 2^16
     ([3000], [300000], 2, 2),                         # P = 2^19
     ([5000], [1 << 20], 2, 1),                        # Jt = 2^20 = P, the largest
@@ -51,10 +53,38 @@ def test_cp_long(fcs, ctx, orc, I, J, R, D):
 
 
 def test_cp_long_chunked_small_budget(fcs, orc):
-    """A 6 MiB budget forces the chunked path (27 of 180 transforms at a time)."""
+    """P = 2^16 under a 6 MiB budget: the chunked path (9 of 180 transforms at a time)."""
     small = fcs.Context(budget=6 << 20)
+    _cp(fcs, None, orc, [150, 120, 100], [20000, 15000, 9000], 20, 3, 42, budget_ctx=small)
+    small.close()
+
+
+@pytest.mark.parametrize("budget", [6 << 20, 2 << 20])
+def test_cp_p15_fused_small_budget(fcs, orc, budget):
+    """P = 2^15 with room for 45 (6 MiB) or 12 (2 MiB) running-product slices:
+    fewer CTAs than the 60 (sketch, rank group) items, each CTA taking several."""
+    small = fcs.Context(budget=budget)
     _cp(fcs, None, orc, [150, 120, 100], [8000, 9000, 7000], 20, 3, 42, budget_ctx=small)
     small.close()
+
+
+def test_cp_p15_invalid_hashes_dropped(fcs, ctx, orc):
+    """Hash values outside [0, J_n) are skipped by the P = 2^15 kernel, as by
+    the count-sketch kernel of the two-pass route: no access leaves the buffer."""
+    I, J, R, D = [90, 80, 70], [9000, 8000, 7000], 4, 2
+    U, lam = synth.cp_factors(47, I, R)
+    ho, so = orc.make_hashes(48, I, J, D)
+    bad = ho.copy()
+    bad[:, 5] = -3                                   # mode 0, entry 5
+    bad[:, I[0] + 7] = J[1]                          # mode 1, entry 7
+    keep = np.ones_like(ho, dtype=bool)
+    keep[:, 5] = keep[:, I[0] + 7] = False
+    U0 = [u.astype(np.float64).copy() for u in U]
+    U0[0][5] = 0.0                                   # the oracle sees those entries as zero
+    U0[1][7] = 0.0
+    ref = orc.fcs_cp(U0, lam.astype(np.float64), J, np.where(keep, ho, 0), so)
+    got = fcs.fcs_sketch_cp(ctx, [cuda(u) for u in U], cuda(lam), J, cuda(bad), cuda(so))
+    assert_sketch_close(host(got), ref)
 
 
 def _contract_case(fcs, ctx, orc, cache: bool):
