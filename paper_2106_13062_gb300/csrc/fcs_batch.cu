@@ -109,7 +109,6 @@ __global__ void batch_transpose_kernel(const TransposeTask *__restrict__ tasks, 
 
 // cp_run / cp13_run's accessors over a problem descriptor (fcs_cp_run.cuh).
 struct BatchView {
-  static constexpr bool kWaitsForInputs = false;     // the chain orders itself
   const BatchProb &P;
   int sb;
   __device__ __forceinline__ int modes() const { return P.N; }
@@ -129,10 +128,20 @@ struct BatchView {
   __device__ __forceinline__ unsigned *ticket(int d) const { return P.tickets + d; }
 };
 
-// The class launches form a chain of programmatic dependent launches: a CTA
-// calls pdl_launch_dependents at its start and pdl_wait_previous at its end,
-// which makes each grid complete after its predecessor, so work queued after
-// the chain waits for all of it.
+// Programmatic dependent launch.  launch_dependents lets the next launch of
+// the chain start once every CTA of this grid has issued it (so every CTA of
+// this grid is already resident: the next grid can never hold the SMs this
+// one still needs).  wait_previous returns once the previous grid of the
+// chain has completed and its writes are visible; called at a CTA's end, it
+// makes each grid complete after its predecessor, so work queued after the
+// chain waits for all of it.  Both are no-ops in a launch made without the
+// programmatic-serialisation attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait_previous() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 
 // One CTA per item (problem, sketch d, rank group) of one FFT-size class,
 // P = 2^(LOG2M+1) <= 8192, NT = 2^(LOG2M-4) threads.

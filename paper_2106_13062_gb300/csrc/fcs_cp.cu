@@ -48,9 +48,6 @@ struct TransposeArgs {
 
 // cp_run / cp13_run's accessors over CpArgs (fcs_cp_run.cuh).
 struct CpView {
-  // prep_kernel, launched just before, writes the columns and clears the
-  // spectrum; the sketch kernels are launched with programmatic serialisation
-  static constexpr bool kWaitsForInputs = true;
   const CpArgs &a;
   int sb;
   __device__ __forceinline__ int modes() const { return a.m.N; }
@@ -105,10 +102,6 @@ struct PrepArgs {
 };
 
 __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a) {
-  // launched with programmatic serialisation: the previous launch may still
-  // read the workspace; the sketch kernel may start its set-up right away
-  pdl_wait_previous();
-  pdl_launch_dependents();
   const int64_t b = blockIdx.x;
   const int tid = threadIdx.x;
   if (b < a.ntile) {
@@ -166,8 +159,8 @@ int launch_cp13(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
   if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp13)");
   const float2 *twp = ctx->twiddle;
   void *args[] = {&a, &twp};
-  e = launch_pdl(kern, dim3(unsigned(groups), unsigned(a.D)), dim3(wdit::kNT), smem, ctx->stream,
-                 args);
+  e = cudaLaunchKernel(kern, dim3(unsigned(groups), unsigned(a.D)), dim3(wdit::kNT), args, smem,
+                       ctx->stream);
   return check_cuda(ctx, e, "cp13_kernel");
 }
 
@@ -185,13 +178,8 @@ int launch_cp(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp)");
       }
-      const float2 *twp = ctx->twiddle;
-      void *args[] = {&a, &twp};
-      return check_cuda(ctx,
-                        launch_pdl(reinterpret_cast<const void *>(kern),
-                                   dim3(unsigned(groups), unsigned(a.D)), dim3(NT), smem,
-                                   ctx->stream, args),
-                        "cp_kernel");
+      kern<<<dim3(unsigned(groups), unsigned(a.D)), NT, smem, ctx->stream>>>(a, ctx->twiddle);
+      return check_cuda(ctx, cudaGetLastError(), "cp_kernel");
     };
     if (cpt <= 1) return go(cp_kernel<LOG2M, NT, 1>);
     if (cpt <= 2) return go(cp_kernel<LOG2M, NT, 2>);
@@ -286,11 +274,8 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
     pa.zero_blocks = int(std::min<int64_t>(64, (pa.zero_n4 + 255) / 256));
     const int64_t blocks = pa.ntile + pa.zero_blocks;
     if (blocks > 0x7fffffffLL) return set_error(ctx, FCS_EUNSUPPORTED, "factor matrices too large");
-    void *args[] = {&pa};
-    rc = check_cuda(ctx,
-                    launch_pdl(reinterpret_cast<const void *>(prep_kernel), dim3(unsigned(blocks)),
-                               dim3(256), 0, ctx->stream, args),
-                    "prep_kernel");
+    prep_kernel<<<unsigned(blocks), 256, 0, ctx->stream>>>(pa);
+    rc = check_cuda(ctx, cudaGetLastError(), "prep_kernel");
     if (rc) return rc;
   }
   rc = FCS_EUNSUPPORTED;

@@ -23,11 +23,7 @@
 //   float *sketch(d), float2 *spectrum() ([D][M + 2] float2, 16-byte
 //   aligned, zero before the first group of a sketch adds into it),
 //   unsigned *ticket(d) (zero at start; reset by the last group), int sb
-//   (scatter-buffer length in floats: max J_n rounded up to 4), and
-//   kWaitsForInputs: true when the factor columns, tables, spectrum and
-//   tickets may come from the previous launch on the stream (programmatic
-//   dependent launch), so the work waits for it after its shared-memory
-//   set-up.
+//   (scatter-buffer length in floats: max J_n rounded up to 4).
 #pragma once
 
 #include "fcs_fft.cuh"
@@ -96,7 +92,6 @@ __device__ __forceinline__ void cp_run(const Prob &a, int d, int64_t r0, int64_t
       }
     }
   };
-  if constexpr (Prob::kWaitsForInputs) pdl_wait_previous();
   fetch(r0, 0);
   __syncthreads();
 
@@ -277,17 +272,12 @@ __device__ __forceinline__ void cp13_run(const Prob &a, int d, int64_t r0, int64
       }
     }
   };
-  // the first column's loads and the twiddle loads overlap (when the inputs
-  // come from the previous launch, the set-up runs while it completes)
-  if constexpr (!Prob::kWaitsForInputs) fetch(r0, 0);
+  // the first column's loads and the twiddle loads overlap
+  fetch(r0, 0);
   wdit::fill_twiddles(tws, tw);
   for (int e = tid; e < 16 * ra; e += NT) A2[e] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc4[q * NT + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-  if constexpr (Prob::kWaitsForInputs) {
-    pdl_wait_previous();
-    fetch(r0, 0);
-  }
   __syncthreads();
   scatter(r0, 0);
   __syncthreads();

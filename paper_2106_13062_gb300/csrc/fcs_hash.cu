@@ -48,10 +48,6 @@ struct HashArgs {
 // One thread per table entry (d, global position e in [0, total)).
 __global__ void make_hashes_kernel(HashArgs a, int32_t *__restrict__ h,
                                    int8_t *__restrict__ s) {
-  // launched with programmatic serialisation: the previous launch may still
-  // read the tables being overwritten
-  pdl_wait_previous();
-  pdl_launch_dependents();
   const int d = blockIdx.y;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < a.total;
        e += int64_t(gridDim.x) * blockDim.x) {
@@ -100,10 +96,6 @@ extern "C" int fcs_make_hashes(fcs_ctx *ctx, uint64_t seed, int N, const int64_t
   const int threads = 256;
   int64_t blocks = (a.total + threads - 1) / threads;
   if (blocks > 65535) blocks = 65535;
-  void *args[] = {&a, &h, &s};
-  return check_cuda(ctx,
-                    launch_pdl(reinterpret_cast<const void *>(make_hashes_kernel),
-                               dim3(unsigned(blocks), unsigned(D)), dim3(threads), 0, ctx->stream,
-                               args),
-                    "make_hashes_kernel");
+  make_hashes_kernel<<<dim3(unsigned(blocks), unsigned(D)), threads, 0, ctx->stream>>>(a, h, s);
+  return check_cuda(ctx, cudaGetLastError(), "make_hashes_kernel");
 }

@@ -450,37 +450,6 @@ __device__ __forceinline__ float median_net(float *v) {
 }
 
 // ---------------------------------------------------------------- launch helpers
-// Programmatic dependent launch.  launch_dependents lets the next launch on
-// the stream start once every CTA of this grid has issued it (so every CTA
-// of this grid is already resident: the next grid can never hold the SMs
-// this one still needs).  wait_previous returns once the previous grid has
-// completed and its writes are visible.  Both are no-ops in a launch made
-// without the programmatic-serialisation attribute.
-__device__ __forceinline__ void pdl_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait_previous() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-// Launch `kern` on `stream` with programmatic stream serialisation: its CTAs
-// may start before the previous launch completes, so the kernel must call
-// pdl_wait_previous before it touches anything that launch may still use.
-// `args` points at the kernel's arguments, as for cudaLaunchKernel.
-inline cudaError_t launch_pdl(const void *kern, dim3 grid, dim3 block, size_t smem,
-                              cudaStream_t stream, void **args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = stream;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, kern, args);
-}
-
 // Runtime LOG2M -> compile-time dispatch for 3 <= LOG2M <= 13.
 #define FCS_DISPATCH_LOG2M(log2m, BODY)                      \
   switch (log2m) {                                           \
