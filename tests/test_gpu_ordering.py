@@ -1,0 +1,174 @@
+"""Stream and graph ordering of the single-problem CP route and of batch
+plans, against the FP64 oracle: back-to-back sketches through one
+workspace, a sketch right after a batch chain (whose kernels release their
+dependents early), inputs copied on another stream, CUDA-graph capture and
+replay with the inputs changed in place between replays, and a graph that
+reads every output of a batch plan right after the plan's launch.  Needs a
+GPU."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_common import assert_sketch_close, cuda, host
+
+pytestmark = pytest.mark.gpu
+
+I, J = [700, 600, 800], [5000, 4000, 6000]      # Jt = 14998, P = 16384 (warp-DIT kernel)
+I2, J2 = [300, 200], [2000, 1500]               # Jt = 3499, P = 4096 (slot-FFT kernel)
+
+
+@pytest.fixture(scope="module")
+def fcs():
+    import paper_2106_13062_gb300 as m
+    m.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(fcs):
+    c = fcs.Context()
+    yield c
+    c.close()
+
+
+def _ref(orc, U, lam, J_, seed, D):
+    ho, so = orc.make_hashes(seed, [u.shape[0] for u in U], J_, D)
+    return orc.fcs_cp([u.astype(np.float64) for u in U], lam.astype(np.float64), J_, ho, so)
+
+
+@pytest.mark.parametrize("shape", [(I, J), (I2, J2)])
+def test_back_to_back_sketches_share_the_workspace(fcs, ctx, orc, shape):
+    """Call k + 1's prep overwrites the transposed factors and the spectrum
+    accumulator that call k's sketch kernel reads: it must wait for it."""
+    Is, Js = shape
+    R, D = 40, 6
+    outs, refs = [], []
+    for k in range(4):
+        U, lam = synth.cp_factors(200 + k, Is, R)
+        h, s = fcs.fcs_make_hashes(ctx, 300 + k, Is, Js, D)
+        outs.append(fcs.fcs_sketch_cp(ctx, [cuda(u) for u in U], cuda(lam), Js, h, s))
+        refs.append(_ref(orc, U, lam, Js, 300 + k, D))
+    for k in range(4):
+        assert_sketch_close(host(outs[k]), refs[k], what=f"call {k}")
+
+
+def test_sketch_right_after_a_batch_chain(fcs, ctx, orc):
+    """The batch class kernels let their dependents launch early.  The batch
+    writes its output straight into the factor matrix of a sketch queued
+    right after the chain, whose prep kernel must wait for the chain."""
+    R, D = 8, 3
+    Ub, lamb = synth.cp_factors(210, [64, 48], 4)
+    hb, sb = fcs.fcs_make_hashes(ctx, 310, [64, 48], [40, 60], 2)
+    keep = [cuda(u) for u in Ub] + [cuda(lamb)]
+    U, lam = synth.cp_factors(211, I, R)
+    Ug = [cuda(u) for u in U]
+    out_b = Ug[0].view(-1)[:2 * 99].view(2, 99)      # Jt = 40 + 60 - 1 = 99
+    p, _ = fcs.cp_problem(keep[:2], keep[2], [40, 60], hb, sb, out=out_b)
+    plan = fcs.BatchPlan(ctx, [p], grain=1)
+    h, s = fcs.fcs_make_hashes(ctx, 311, I, J, D)
+    lamg = cuda(lam)
+    for _ in range(3):
+        plan.launch()
+        got = fcs.fcs_sketch_cp(ctx, Ug, lamg, J, h, s)
+    ref_b = orc.fcs_cp([u.astype(np.float64) for u in Ub], lamb.astype(np.float64), [40, 60],
+                       host(hb), host(sb))
+    assert_sketch_close(host(out_b), ref_b, what="batch output")
+    U0 = host(Ug[0]).copy()
+    assert_sketch_close(host(got), _ref(orc, [U0, U[1], U[2]], lam, J, 311, D),
+                        what="sketch after chain")
+    plan.close()
+
+
+def test_inputs_copied_on_another_stream(fcs, ctx, orc):
+    """The factors arrive by a copy on a side stream that the main stream
+    waits for; the hash kernel runs meanwhile, the prep kernel after both."""
+    R, D = 60, 5
+    U, lam = synth.cp_factors(220, I, R)
+    hostbuf = torch.from_numpy(np.concatenate([u.reshape(-1) for u in U])).pin_memory()
+    dev = torch.full(hostbuf.shape, float("nan"), device="cuda")
+    offs = np.cumsum([0] + [u.size for u in U])
+    Ud = [dev[offs[n]:offs[n + 1]].view(I[n], R) for n in range(3)]
+    side = torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+    side.wait_stream(main)
+    with torch.cuda.stream(side):
+        dev.copy_(hostbuf, non_blocking=True)
+    h, s = fcs.fcs_make_hashes(ctx, 320, I, J, D)
+    main.wait_stream(side)
+    got = fcs.fcs_sketch_cp(ctx, Ud, cuda(lam), J, h, s)
+    assert_sketch_close(host(got), _ref(orc, U, lam, J, 320, D), what="side-stream inputs")
+
+
+def test_graph_capture_and_replay(fcs, ctx, orc):
+    """make_hashes + sketch captured into one CUDA graph (programmatic edges)
+    and replayed on new factor values in the same buffers."""
+    R, D = 30, 4
+    U, lam = synth.cp_factors(230, I, R)
+    Ug = [cuda(u) for u in U]
+    lamg = cuda(lam)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        h, s = fcs.fcs_make_hashes(ctx, 330, I, J, D)      # warm: workspace sized
+        out = fcs.fcs_sketch_cp(ctx, Ug, lamg, J, h, s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=st):
+            h2, s2 = fcs.fcs_make_hashes(ctx, 331, I, J, D)
+            fcs.fcs_sketch_cp(ctx, Ug, lamg, J, h2, s2, out=out)
+    for u in Ug:
+        u.mul_(-0.5)
+    g.replay()
+    torch.cuda.synchronize()
+    Un = [u * -0.5 for u in U]
+    assert_sketch_close(host(out), _ref(orc, Un, lam, J, 331, D), what="graph replay")
+    for u in Ug:
+        u.mul_(-2.0)                       # back to the original values
+    g.replay()
+    torch.cuda.synchronize()
+    assert_sketch_close(host(out), _ref(orc, U, lam, J, 331, D), what="second replay")
+    torch.cuda.current_stream().wait_stream(st)
+
+
+def test_graph_reads_batch_outputs_after_the_chain(fcs, ctx, orc):
+    """A graph that launches a batch plan (one class kernel per FFT size,
+    chained) and then copies every output: the copies must see every class
+    finished, not only the last one."""
+    shapes = [([300, 200, 250], [5000, 4000, 6000], 40, 4),   # P = 16384 (longest class)
+              ([100, 120], [2000, 1500], 8, 3),               # P = 4096
+              ([50, 40], [300, 200], 4, 2)]                   # P = 512 (last, short)
+    probs, refs, keep = [], [], []
+    for k, (Is, Js, R, D) in enumerate(shapes):
+        U, lam = synth.cp_factors(240 + k, Is, R)
+        ho, so = orc.make_hashes(340 + k, Is, Js, D)
+        kk = [cuda(u) for u in U] + [cuda(lam), cuda(ho), cuda(so)]
+        p, out = fcs.cp_problem(kk[:len(U)], kk[-3], Js, kk[-2], kk[-1])
+        probs.append(p)
+        keep.append((kk, out))
+        refs.append(orc.fcs_cp([u.astype(np.float64) for u in U], lam.astype(np.float64), Js,
+                               ho, so))
+    plan = fcs.BatchPlan(ctx, probs, grain=2)
+    snaps = [torch.empty_like(out) for _, out in keep]
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        plan.launch()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=st):
+            plan.launch()
+            for snap, (_, out) in zip(snaps, keep):
+                snap.copy_(out)
+    torch.cuda.current_stream().wait_stream(st)
+    for _ in range(3):
+        for (_, out), snap in zip(keep, snaps):
+            out.zero_()
+            snap.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for k, (snap, ref) in enumerate(zip(snaps, refs)):
+            assert_sketch_close(host(snap), ref, what=f"graph snapshot {k}")
+    plan.close()
