@@ -30,7 +30,10 @@
  *    unspecified.  FFT-based calls (CP route, contractions,
  *    outer combine) need Jt <= 2^20: the FFT length is P = smallest power of
  *    two >= Jt, 16 <= P <= 2^20, else FCS_EUNSUPPORTED.  P <= 16384 runs one
- *    transform per CTA in shared memory; longer transforms use a two-pass
+ *    transform per CTA in shared memory.  The CP route at P = 32768 runs one
+ *    fused kernel (one 2^14-point transform per CTA in shared memory, a
+ *    128 KiB running-product slice per CTA in the context workspace, fewer
+ *    CTAs when the budget is small).  Other longer transforms use a two-pass
  *    FFT through the context workspace (at most min(budget, 512 MiB), work
  *    split into chunks that fit; a few MiB suffice).  fcs_sketch_cp_noalloc
  *    and the persistent batch kernel take P <= 16384 (batch plans run longer
