@@ -1,6 +1,7 @@
 """Stream and graph ordering of the single-problem CP route and of batch
 plans, against the FP64 oracle: back-to-back sketches through one
-workspace, a sketch right after a batch chain (whose kernels release their
+workspace, the context's spectrum accumulator left zero across calls of
+different shapes, a sketch right after a batch chain (whose kernels release their
 dependents early), inputs copied on another stream, CUDA-graph capture and
 replay with the inputs changed in place between replays, and a graph that
 reads every output of a batch plan right after the plan's launch.  Needs a
@@ -53,6 +54,25 @@ def test_back_to_back_sketches_share_the_workspace(fcs, ctx, orc, shape):
         refs.append(_ref(orc, U, lam, Js, 300 + k, D))
     for k in range(4):
         assert_sketch_close(host(outs[k]), refs[k], what=f"call {k}")
+
+
+def test_accumulator_left_zero_across_shapes(fcs, orc):
+    """The spectrum accumulator and tickets are cleared by the kernels that
+    used them, not before each call: a sequence of calls with every FFT
+    length and sketch count mixed, on a fresh context, each against the
+    oracle."""
+    c = fcs.Context()
+    seq = [([700, 600, 800], [5000, 4000, 6000], 30, 16),    # P = 16384, D = 16
+           ([20, 30], [10, 12], 3, 1),                        # P = 32
+           ([300, 200], [2000, 1500], 12, 9),                 # P = 4096
+           ([700, 600, 800], [5000, 4000, 6000], 7, 3),       # P = 16384 again
+           ([40, 50, 60], [300, 200, 100], 5, 16)]            # P = 1024
+    for k, (Is, Js, R, D) in enumerate(seq):
+        U, lam = synth.cp_factors(250 + k, Is, R)
+        h, s = fcs.fcs_make_hashes(c, 350 + k, Is, Js, D)
+        got = fcs.fcs_sketch_cp(c, [cuda(u) for u in U], cuda(lam), Js, h, s)
+        assert_sketch_close(host(got), _ref(orc, U, lam, Js, 350 + k, D), what=f"call {k}")
+    c.close()
 
 
 def test_sketch_right_after_a_batch_chain(fcs, ctx, orc):
