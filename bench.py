@@ -174,7 +174,7 @@ class CpWorkload:
         return self.D
 
     def launches_per_step(self):
-        return 2                     # hashes, sketch kernel
+        return 3                     # hashes, prep (transpose + clear), sketch kernel
 
     def flops(self):
         """2.5 P log2 P per real FFT of length P (D*R*N forward + D inverse)
@@ -247,7 +247,7 @@ class CpWorkload:
         peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
         ach = self.flops() / (t / 1e3) / 1e12
         files = ["fcs_cp.cu", "fcs_cp_run.cuh", "fcs_fft.cuh", "fcs_internal.cuh"]
-        return {"kernel": "cp13_kernel (fcs_sketch_cp: the fused sketch, one launch)",
+        return {"kernel": "cp13_kernel (fcs_sketch_cp: prep launch + fused sketch)",
                 "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak,
                 "traffic": profiled_traffic("cp_kernel_order3_I1000_R100_J5000_D10.txt", files),

@@ -40,8 +40,7 @@
  *    problems with their own launches).
  *  - The library allocates only its own context workspace (device memory
  *    reused across calls, bounded by the context's budget), a 256 KiB
- *    twiddle table, a 1 MiB CP-route spectrum accumulator (zero between
- *    calls) and, when enabled, the spectrum cache of fcs_contract.
+ *    twiddle table and, when enabled, the spectrum cache of fcs_contract.
  *    A context must be used from one host thread at a time.
  *  - Floating point is FP32 throughout; sums use atomics, so the last bits
  *    of a result may differ from run to run.  Hashes and bins are exact.
@@ -139,9 +138,7 @@ int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
  * paper's sum of inverse transforms) and one inverse FFT per sketch.
  *   host_U[N]: device pointers; U_n is I_n x R FP32 row-major with leading
  *   dimension host_ldU[n] >= R.  lambda [R] FP32 or NULL (all ones).
- *   out [D][Jt] FP32.  For P <= 16384 one kernel launch, no workspace (the
- *   spectra go through the context's accumulator); longer P as described
- *   at the top of this file.
+ *   out [D][Jt] FP32.  Needs D*(P/2+1)*8 + 64 bytes of workspace.
  */
 int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
                   const int32_t *host_J, int64_t R, int D,
@@ -157,17 +154,17 @@ int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
  * where the implicit device synchronisation of cudaMalloc / cudaFree would
  * stall other work, and processes whose device memory is fixed at start-up.
  * This entry point needs no fcs_ctx and allocates nothing: its scratch is a
- * file-scope __device__ array of about 1 MiB (the spectrum accumulator for
- * 16 sketches at P = 16384 and their tickets; the factor columns are read in
- * place) plus a 256 KiB twiddle table, which every GPU loading the library
- * holds until the process exits.
+ * file-scope __device__ array of 4 MiB (plus a 256 KiB twiddle table) that
+ * every GPU loading the library holds until the process exits.
  *   - Runs on the calling thread's current device, on `stream`.
- *   - The first call on a device looks up the arrays' device addresses, fills
- *     the twiddle table and zeroes the scratch, synchronising `stream` once;
- *     make that first call before any stream capture.
+ *   - The first call on a device looks up the arrays' device addresses and
+ *     fills the twiddle table, synchronising `stream` once; make that first
+ *     call before any stream capture.
+ *   - Problems whose scratch D*(P/2+1)*8 + 512 + R*sum(I_n)*4 bytes exceed
+ *     4 MiB are rejected with FCS_ENOMEM_BUDGET (nothing is launched).
  *   - All calls share the one array: calls that overlap on the GPU (other
  *     streams, other host threads) race and corrupt each other's results.
- *     Every call leaves the scratch zero for the next.
+ *     Each call clears the parts that must start at zero.
  *   - err (may be NULL) receives a message of at most err_len bytes.
  * Arguments and output otherwise as fcs_sketch_cp.
  */

@@ -116,9 +116,6 @@ struct BatchView {
   __device__ __forceinline__ const float *column(int n, int64_t r) const {
     return P.UT + P.ut_off[n] + r * P.I[n];
   }
-  // the batched transpose lays the columns out contiguously, lambda folded in
-  __device__ __forceinline__ int64_t col_stride(int) const { return 1; }
-  __device__ __forceinline__ float col_scale(int, int64_t) const { return 1.f; }
   __device__ __forceinline__ const int32_t *hashes(int d, int n) const {
     return P.h + d * P.ldh + P.off[n];
   }

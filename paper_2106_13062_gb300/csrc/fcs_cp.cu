@@ -3,15 +3,16 @@
 // with P the smallest power of two >= Jt (any P >= Jt gives the exact linear
 // convolution, so out = the first Jt samples).
 //
-// One kernel: CTA (g, d) owns sketch d and a contiguous group of ranks and
-// runs cp_run (P <= 8192) or cp13_run (P = 16384) of fcs_cp_run.cuh: count
-// sketch of each factor column (read straight from U_n with its row stride,
-// lambda_r applied on mode 1), block real FFT, mode product and rank sum in
-// the frequency domain (linearity moves the paper's sum of inverse
-// transforms inside one inverse transform), partial spectrum into the
-// context's accumulator, and the one inverse FFT by the CTA that completes
-// sketch d, which leaves the accumulator and its ticket zero for the next
-// call.  Longer transforms go to the routes of fcs_big.cu.
+// Two kernels.  (1) prep_kernel writes the factor columns contiguously
+// (lambda folded into mode 1) so every column load is coalesced, and clears
+// the spectrum accumulator.  (2) The fused sketch kernel: CTA (g, d) owns
+// sketch d and a contiguous group of ranks and runs cp_run (P <= 8192) or
+// cp13_run (P = 16384) of fcs_cp_run.cuh: count sketch, block real FFT, mode
+// product and rank sum in the frequency domain (linearity moves the paper's
+// sum of inverse transforms inside one inverse transform), partial spectrum
+// into a global accumulator, and the one inverse FFT by the CTA that
+// completes sketch d.  Longer transforms go to the two-pass route of
+// fcs_big.cu.
 #include <algorithm>
 #include <cstdarg>
 #include <mutex>
@@ -26,15 +27,23 @@ struct CpArgs {
   int D;
   int64_t R;
   int64_t ranks_per_cta;
-  const float *U[kMaxN]; // U_n: I_n x R, row-major with leading dimension ldU[n]
-  int64_t ldU[kMaxN];
-  const float *lambda;   // [R] or null
+  const float *UT;       // [sum_n R*I_n]: mode n column r at ut_off[n] + r*I_n
+  int64_t ut_off[kMaxN];
   const int32_t *h;
   const int8_t *s;
-  float2 *G;             // [D][M+2] spectrum accumulator (bins 0..M), zero at launch
+  float2 *G;             // [D][M+2] spectrum accumulator (bins 0..M), zeroed per call
   unsigned *counter;     // [D] tickets, zero at launch, reset by the last CTA
   float *out;            // [D][Jt]
   int sb;                // scatter buffer length (floats): max J_n rounded up to 4
+};
+
+// All modes in one launch: mode n = blockIdx.z.
+struct TransposeArgs {
+  const float *U[kMaxN];
+  int64_t I[kMaxN], ld[kMaxN], ut_off[kMaxN];
+  int64_t R;
+  const float *lambda;
+  float *UT;
 };
 
 // cp_run / cp13_run's accessors over CpArgs (fcs_cp_run.cuh).
@@ -43,12 +52,8 @@ struct CpView {
   int sb;
   __device__ __forceinline__ int modes() const { return a.m.N; }
   __device__ __forceinline__ int64_t dim(int n) const { return a.m.I[n]; }
-  // column r of U_n: strided loads, which L2 serves (the factors stay
-  // resident: every sketch reads the same columns)
-  __device__ __forceinline__ const float *column(int n, int64_t r) const { return a.U[n] + r; }
-  __device__ __forceinline__ int64_t col_stride(int n) const { return a.ldU[n]; }
-  __device__ __forceinline__ float col_scale(int n, int64_t r) const {
-    return (n == 0 && a.lambda) ? __ldg(a.lambda + r) : 1.f;
+  __device__ __forceinline__ const float *column(int n, int64_t r) const {
+    return a.UT + a.ut_off[n] + r * a.m.I[n];
   }
   __device__ __forceinline__ const int32_t *hashes(int d, int n) const {
     return a.h + d * a.m.ldh + a.m.off[n];
@@ -83,6 +88,52 @@ __global__ void __launch_bounds__(wdit::kNT) cp13_kernel(CpArgs a, const float2 
   const int64_t r1 = min(a.R, r0 + a.ranks_per_cta);
   const CpView view{a, a.sb};
   cp13_run<CPT, RMAX>(view, blockIdx.y, r0, r1, gridDim.x, smem_raw, tw, &is_last);
+}
+
+// prep_kernel: in one launch, the factor transpose in 32 x 32 tiles,
+// UT[n][r][i] = U_n[i*ld + r] (times lambda_r for n = 0), and the clearing
+// of the spectrum accumulator and tickets.  256 threads per block.
+struct PrepArgs {
+  TransposeArgs t;
+  int64_t tiles_x, tiles_y, ntile;     // transpose tiles per mode and in total
+  float4 *zero;
+  int64_t zero_n4;
+  int zero_blocks;
+};
+
+__global__ void __launch_bounds__(256) prep_kernel(PrepArgs a) {
+  const int64_t b = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (b < a.ntile) {
+    __shared__ float tile[32][33];
+    const int64_t per = a.tiles_x * a.tiles_y;
+    const int n = int(b / per);
+    const int64_t rem = b % per;
+    const int64_t bx = rem % a.tiles_x, by = rem / a.tiles_x;
+    const int64_t I = a.t.I[n], R = a.t.R, ld = a.t.ld[n];
+    const float *U = a.t.U[n];
+    const float *lambda = n == 0 ? a.t.lambda : nullptr;
+    float *UT = a.t.UT + a.t.ut_off[n];
+    const int64_t i0 = bx * 32, rr0 = by * 32;
+    if (i0 >= I) return;
+    const int tx = tid & 31, ty = tid >> 5;
+    for (int k = ty; k < 32; k += 8) {
+      const int64_t i = i0 + k, r = rr0 + tx;
+      if (i < I && r < R) tile[k][tx] = U[i * ld + r];
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+      const int64_t r = rr0 + k, i = i0 + tx;
+      if (i < I && r < R) {
+        const float lam = lambda ? __ldg(lambda + r) : 1.f;
+        UT[r * I + i] = tile[tx][k] * lam;
+      }
+    }
+    return;
+  }
+  const int64_t zb = b - a.ntile;
+  for (int64_t e = zb * 256 + tid; e < a.zero_n4; e += int64_t(a.zero_blocks) * 256)
+    a.zero[e] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Kernel for the given prefetch depth and scatter-buffer height.
@@ -170,6 +221,7 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
     return big_sketch_cp(ctx, a.m, R, D, host_U, host_ldU, lambda, h, s, out, log2p);
   }
   const int log2m = log2p - 1;
+  const int M = 1 << log2m;
   a.D = D;
   a.R = R;
   a.h = h;
@@ -182,21 +234,50 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
   a.ranks_per_cta = (R + groups - 1) / groups;
   groups = (R + a.ranks_per_cta - 1) / a.ranks_per_cta;
 
-  int64_t Imax = 0, Jmax = 0;
+  int64_t Imax = 0, Jmax = 0, utlen = 0;
   for (int n = 0; n < N; ++n) {
-    a.U[n] = host_U[n];
-    a.ldU[n] = host_ldU[n];
+    a.ut_off[n] = utlen;
+    utlen += R * host_I[n];
     if (host_I[n] > Imax) Imax = host_I[n];
     if (host_J[n] > Jmax) Jmax = host_J[n];
   }
-  a.lambda = lambda;
   a.sb = int((Jmax + 3) / 4 * 4);
-  // the context's accumulator: spectra [D][M+2] from its start, the tickets
-  // at a fixed offset (all of it zero between calls)
-  a.G = ctx->cp_acc;
-  a.counter = reinterpret_cast<unsigned *>(ctx->cp_acc + kCpAccPairs);
+  const size_t gbytes = (sizeof(float2) * size_t(D) * size_t(M + 2) + 255) & ~size_t(255);
+  const size_t cbytes = 256;
+  void *ws = nullptr;
+  rc = ensure_workspace(ctx, gbytes + cbytes + sizeof(float) * size_t(utlen), &ws);
+  if (rc) return rc;
+  a.G = static_cast<float2 *>(ws);
+  a.counter = reinterpret_cast<unsigned *>(static_cast<char *>(ws) + gbytes);
+  float *UT = reinterpret_cast<float *>(static_cast<char *>(ws) + gbytes + cbytes);
+  a.UT = UT;
   DeviceGuard g(ctx->device);
   spec_cache_invalidate(ctx, out, sizeof(float) * size_t(D) * size_t(a.m.Jt));
+  {
+    // one launch: factor transpose (lambda folded into mode 1) and clearing
+    // of the accumulator and tickets
+    PrepArgs pa{};
+    for (int n = 0; n < N; ++n) {
+      pa.t.U[n] = host_U[n];
+      pa.t.I[n] = host_I[n];
+      pa.t.ld[n] = host_ldU[n];
+      pa.t.ut_off[n] = a.ut_off[n];
+    }
+    pa.t.R = R;
+    pa.t.lambda = lambda;
+    pa.t.UT = UT;
+    pa.tiles_x = (Imax + 31) / 32;
+    pa.tiles_y = (R + 31) / 32;
+    pa.ntile = pa.tiles_x * pa.tiles_y * N;
+    pa.zero = static_cast<float4 *>(ws);
+    pa.zero_n4 = int64_t(gbytes + cbytes) / 16;
+    pa.zero_blocks = int(std::min<int64_t>(64, (pa.zero_n4 + 255) / 256));
+    const int64_t blocks = pa.ntile + pa.zero_blocks;
+    if (blocks > 0x7fffffffLL) return set_error(ctx, FCS_EUNSUPPORTED, "factor matrices too large");
+    prep_kernel<<<unsigned(blocks), 256, 0, ctx->stream>>>(pa);
+    rc = check_cuda(ctx, cudaGetLastError(), "prep_kernel");
+    if (rc) return rc;
+  }
   rc = FCS_EUNSUPPORTED;
   FCS_DISPATCH_LOG2M(log2m, rc = launch_cp<L>(ctx, a, groups, Imax));
   return rc;
@@ -204,14 +285,15 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
 
 // ---------------------------------------------------------------------------
 // fcs_sketch_cp_noalloc: the CP-route sketch for callers that cannot allocate
-// device memory.  It runs the same kernel as fcs_sketch_cp, but its
-// accumulator (spectra and tickets, laid out as a context's) and its twiddle
-// table live in file-scope __device__ arrays of fixed size, so the call makes
-// no cudaMalloc / cudaFree and needs no fcs_ctx.
+// device memory.  It runs the same two kernels as fcs_sketch_cp, but its
+// scratch (spectrum accumulator, tickets, transposed factor columns) and its
+// twiddle table live in file-scope __device__ arrays of fixed size instead of
+// a context workspace, so the call makes no cudaMalloc / cudaFree and needs
+// no fcs_ctx.
 namespace fcs {
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = kCpAccBytes;       // about 1 MiB
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;   // 4 MiB
 constexpr int kNoAllocMaxDevices = 64;
 
 // One copy of each array exists on every GPU that loads the library and is
@@ -273,8 +355,6 @@ int noalloc_setup(int dev, cudaStream_t st, NoAllocDevice **out, char *err, size
       return noalloc_fail(err, n, FCS_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
     noalloc_twiddle_kernel<<<kTwN / 256, 256, 0, st>>>(s.twiddle);
     e = cudaGetLastError();
-    // the accumulator and tickets start at zero; every call leaves them zero
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.scratch, 0, kNoAllocScratchBytes, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
       return noalloc_fail(err, n, FCS_ECUDA, "twiddle set-up: %s", cudaGetErrorString(e));
@@ -352,14 +432,22 @@ extern "C" int fcs_sketch_cp_noalloc(void *stream, int N, const int64_t *host_I,
     return noalloc_fail(err, err_len, FCS_EUNSUPPORTED, "Jt=%lld needs FFT length > %d",
                         (long long)a.m.Jt, 1 << kMaxLog2P);
   const int log2m = log2p - 1;
-  int64_t Imax = 0, Jmax = 0;
+  const int M = 1 << log2m;
+  int64_t Imax = 0, Jmax = 0, utlen = 0;
   for (int n = 0; n < N; ++n) {
-    a.U[n] = host_U[n];
-    a.ldU[n] = host_ldU[n];
+    a.ut_off[n] = utlen;
+    utlen += R * host_I[n];
     if (host_I[n] > Imax) Imax = host_I[n];
     if (host_J[n] > Jmax) Jmax = host_J[n];
   }
-  a.lambda = lambda;
+  const size_t gbytes = (sizeof(float2) * size_t(D) * size_t(M + 2) + 255) & ~size_t(255);
+  const size_t cbytes = 256;
+  const size_t need = gbytes + cbytes + sizeof(float) * size_t(utlen);
+  if (need > kNoAllocScratchBytes)
+    return noalloc_fail(err, err_len, FCS_ENOMEM_BUDGET,
+                        "problem needs %zu bytes of scratch; the static scratch array holds "
+                        "%zu bytes (D*(P/2+1)*8 + R*sum(I_n)*4 must fit)",
+                        need, kNoAllocScratchBytes);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess)
@@ -382,10 +470,34 @@ extern "C" int fcs_sketch_cp_noalloc(void *stream, int N, const int64_t *host_I,
   if (groups > R) groups = R;
   a.ranks_per_cta = (R + groups - 1) / groups;
   groups = (R + a.ranks_per_cta - 1) / a.ranks_per_cta;
-  // the same layout as a context's accumulator; zeroed at set-up and left
-  // zero by every call
   a.G = reinterpret_cast<float2 *>(sd->scratch);
-  a.counter = reinterpret_cast<unsigned *>(sd->scratch + kCpAccPairs * sizeof(float2));
+  a.counter = reinterpret_cast<unsigned *>(sd->scratch + gbytes);
+  float *UT = reinterpret_cast<float *>(sd->scratch + gbytes + cbytes);
+  a.UT = UT;
+  // the accumulator and tickets must start at zero (the array keeps the
+  // previous call's contents); the same launch transposes the factors
+  {
+    PrepArgs pa{};
+    for (int n = 0; n < N; ++n) {
+      pa.t.U[n] = host_U[n];
+      pa.t.I[n] = host_I[n];
+      pa.t.ld[n] = host_ldU[n];
+      pa.t.ut_off[n] = a.ut_off[n];
+    }
+    pa.t.R = R;
+    pa.t.lambda = lambda;
+    pa.t.UT = UT;
+    pa.tiles_x = (Imax + 31) / 32;
+    pa.tiles_y = (R + 31) / 32;
+    pa.ntile = pa.tiles_x * pa.tiles_y * N;
+    pa.zero = reinterpret_cast<float4 *>(sd->scratch);
+    pa.zero_n4 = int64_t(gbytes + cbytes) / 16;
+    pa.zero_blocks = int(std::min<int64_t>(64, (pa.zero_n4 + 255) / 256));
+    prep_kernel<<<unsigned(pa.ntile + pa.zero_blocks), 256, 0, st>>>(pa);
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+      return noalloc_fail(err, err_len, FCS_ECUDA, "prep: %s", cudaGetErrorString(e));
+  }
   rc = FCS_EUNSUPPORTED;
   FCS_DISPATCH_LOG2M(log2m, rc = noalloc_launch_cp<L>(a, groups, Imax, sd->twiddle, st, err,
                                                       err_len));

@@ -18,13 +18,10 @@
 //                        512 threads, two block barriers per transform).
 //
 // The problem is read through a small accessor interface (Prob):
-//   int modes(), int64_t dim(n), const float *column(n, r) (entry i of the
-//   factor column at column(n, r)[i * col_stride(n)]), float col_scale(n, r)
-//   (a factor on the whole column: lambda_r on mode 1, or 1),
+//   int modes(), int64_t dim(n), const float *column(n, r),
 //   const int32_t *hashes(d, n), const int8_t *signs(d, n), int64_t length(),
 //   float *sketch(d), float2 *spectrum() ([D][M + 2] float2, 16-byte
-//   aligned, zero before the first group of a sketch adds into it; the last
-//   group zeroes what it read, so it is zero again when the call ends),
+//   aligned, zero before the first group of a sketch adds into it),
 //   unsigned *ticket(d) (zero at start; reset by the last group), int sb
 //   (scatter-buffer length in floats: max J_n rounded up to 4).
 #pragma once
@@ -81,8 +78,6 @@ __device__ __forceinline__ void cp_run(const Prob &a, int d, int64_t r0, int64_t
   auto fetch = [&](int64_t r, int n) {
     const int64_t In = a.dim(n);
     const float *col = a.column(n, r);
-    const int64_t cs = a.col_stride(n);
-    const float w = a.col_scale(n, r);
     const int32_t *hn = a.hashes(d, n);
     const int8_t *sn = a.signs(d, n);
 #pragma unroll
@@ -91,7 +86,7 @@ __device__ __forceinline__ void cp_run(const Prob &a, int d, int64_t r0, int64_t
       ph[c] = -1;
       pv[c] = 0.f;
       if (i < In) {
-        const float v = __ldg(col + i * cs) * w;
+        const float v = __ldg(col + i);
         pv[c] = __ldg(sn + i) < 0 ? -v : v;
         ph[c] = __ldg(hn + i);
       }
@@ -110,13 +105,11 @@ __device__ __forceinline__ void cp_run(const Prob &a, int d, int64_t r0, int64_t
       if (In > int64_t(CPT) * NT) {
         // entries beyond the prefetched chunk: load and scatter directly
         const float *col = a.column(n, r);
-        const int64_t cs = a.col_stride(n);
-        const float w = a.col_scale(n, r);
         const int32_t *hn = a.hashes(d, n);
         const int8_t *sn = a.signs(d, n);
         for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
           const int hb = __ldg(hn + i);
-          const float v = __ldg(col + i * cs) * w;
+          const float v = __ldg(col + i);
           if (unsigned(hb) < unsigned(sb)) atomicAdd(A + hb, __ldg(sn + i) < 0 ? -v : v);
         }
       }
@@ -187,18 +180,12 @@ __device__ __forceinline__ void cp_run(const Prob &a, int d, int64_t r0, int64_t
   // last group for sketch d: one inverse real FFT of the summed spectrum
   for (int q = tid; q < HALF; q += NT) {
     float2 Av, Bv;
-    const float2 z = make_float2(0.f, 0.f);
     if (q == 0) {
       Av = make_float2(__ldcg(&Gd[0].x), __ldcg(&Gd[M].x));
       Bv = __ldcg(&Gd[HALF]);
-      Gd[0] = z;                       // leave the accumulator zero
-      Gd[M] = z;
-      Gd[HALF] = z;
     } else {
       Av = __ldcg(&Gd[q]);
       Bv = __ldcg(&Gd[M - q]);
-      Gd[q] = z;
-      Gd[M - q] = z;
     }
     pack_pair_conj<LOG2M>(B, q, Av, Bv, tw);
   }
@@ -253,8 +240,6 @@ __device__ __forceinline__ void cp13_run(const Prob &a, int d, int64_t r0, int64
   auto fetch = [&](int64_t r, int n) {
     const int64_t In = a.dim(n);
     const float *col = a.column(n, r);
-    const int64_t cs = a.col_stride(n);
-    const float w = a.col_scale(n, r);
     const int32_t *hn = a.hashes(d, n);
     const int8_t *sn = a.signs(d, n);
 #pragma unroll
@@ -263,7 +248,7 @@ __device__ __forceinline__ void cp13_run(const Prob &a, int d, int64_t r0, int64
       ph[c] = -1;
       pv[c] = 0.f;
       if (i < In) {
-        const float v = __ldg(col + i * cs) * w;
+        const float v = __ldg(col + i);
         pv[c] = __ldg(sn + i) < 0 ? -v : v;
         ph[c] = __ldg(hn + i);
       }
@@ -277,13 +262,11 @@ __device__ __forceinline__ void cp13_run(const Prob &a, int d, int64_t r0, int64
     const int64_t In = a.dim(n);
     if (In > int64_t(CPT) * NT) {
       const float *col = a.column(n, r);
-      const int64_t cs = a.col_stride(n);
-      const float w = a.col_scale(n, r);
       const int32_t *hn = a.hashes(d, n);
       const int8_t *sn = a.signs(d, n);
       for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
         const int hb = __ldg(hn + i);
-        const float v = __ldg(col + i * cs) * w;
+        const float v = __ldg(col + i);
         if (unsigned(hb) < unsigned(sb))
           atomicAdd(A + wdit::a_index(hb, ra), __ldg(sn + i) < 0 ? -v : v);
       }
@@ -391,20 +374,6 @@ __device__ __forceinline__ void cp13_run(const Prob &a, int d, int64_t r0, int64
         Av[k] = __ldcg(&Gd[q]);
         Bv[k] = __ldcg(&Gd[M - q]);
         Wv[k] = __ldg(&tw[q << (kLogTwN - wdit::kL - 1)]);   // W_P^q
-      }
-    }
-    // leave the accumulator zero (each thread clears what it read)
-    const float2 z = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int q = k * NT + tid;
-      if (q == 0) {
-        Gd[0] = z;
-        Gd[M] = z;
-        Gd[HALF] = z;
-      } else {
-        Gd[q] = z;
-        Gd[M - q] = z;
       }
     }
 #pragma unroll

@@ -149,21 +149,10 @@ extern "C" int fcs_create(fcs_ctx **out, int device, void *stream, size_t budget
     delete ctx;
     return FCS_ECUDA;
   }
-  e = cudaMalloc(&ctx->cp_acc, kCpAccBytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(ctx->twiddle);
-    delete ctx;
-    return FCS_ECUDA;
-  }
   twiddle_kernel<<<kTwN / 256, 256, 0, ctx->stream>>>(ctx->twiddle);
   rc = check_cuda(ctx, cudaGetLastError(), "twiddle_kernel");
-  if (rc == FCS_OK)
-    rc = check_cuda(ctx, cudaMemsetAsync(ctx->cp_acc, 0, kCpAccBytes, ctx->stream),
-                    "cudaMemsetAsync(cp_acc)");
   if (rc == FCS_OK) rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "twiddle sync");
   if (rc != FCS_OK) {
-    cudaFree(ctx->cp_acc);
     cudaFree(ctx->twiddle);
     delete ctx;
     return rc;
@@ -182,7 +171,6 @@ extern "C" int fcs_destroy(fcs_ctx *ctx) {
   if (ctx->raw) cudaFree(ctx->raw);
   if (ctx->algo) cudaFree(ctx->algo);
   if (ctx->twiddle) cudaFree(ctx->twiddle);
-  if (ctx->cp_acc) cudaFree(ctx->cp_acc);
   delete ctx;
   return FCS_OK;
 }

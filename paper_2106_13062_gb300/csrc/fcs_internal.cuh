@@ -38,7 +38,6 @@ struct fcs_ctx {
   size_t raw_bytes = 0;
   void *algo = nullptr;          // scratch of fcs_rtpm / fcs_als
   size_t algo_bytes = 0;
-  float2 *cp_acc = nullptr;      // CP-route spectra and tickets, zero between calls
   std::string err;
 };
 
@@ -51,11 +50,6 @@ constexpr int kMaxD = 16;
 constexpr int kMaxLog2P = 14;          // FFT length P <= 16384 in one CTA
 constexpr int kMaxLog2PBig = 20;       // longer transforms through global memory
 constexpr int kMinLog2P = 4;
-// The context's CP-route accumulator (fcs_cp.cu): [kMaxD][P/2 + 2] float2 for
-// the largest in-CTA P, then kMaxD tickets at a fixed offset.  The kernels
-// leave every entry zero when a call ends, so no call has to clear it.
-constexpr size_t kCpAccPairs = size_t(kMaxD) * ((size_t(1) << (kMaxLog2P - 1)) + 2);
-constexpr size_t kCpAccBytes = kCpAccPairs * 8 + 256;
 
 int set_error(fcs_ctx *ctx, int code, const char *fmt, ...);
 void batch_state_destroy(fcs_ctx *ctx);

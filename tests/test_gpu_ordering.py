@@ -1,7 +1,7 @@
 """Stream and graph ordering of the single-problem CP route and of batch
 plans, against the FP64 oracle: back-to-back sketches through one
-workspace, the context's spectrum accumulator left zero across calls of
-different shapes, a sketch right after a batch chain (whose kernels release their
+workspace, calls of different shapes one after another on a fresh
+context, a sketch right after a batch chain (whose kernels release their
 dependents early), inputs copied on another stream, CUDA-graph capture and
 replay with the inputs changed in place between replays, and a graph that
 reads every output of a batch plan right after the plan's launch.  Needs a
@@ -56,11 +56,10 @@ def test_back_to_back_sketches_share_the_workspace(fcs, ctx, orc, shape):
         assert_sketch_close(host(outs[k]), refs[k], what=f"call {k}")
 
 
-def test_accumulator_left_zero_across_shapes(fcs, orc):
-    """The spectrum accumulator and tickets are cleared by the kernels that
-    used them, not before each call: a sequence of calls with every FFT
-    length and sketch count mixed, on a fresh context, each against the
-    oracle."""
+def test_calls_of_mixed_shapes_in_a_row(fcs, orc):
+    """The spectrum accumulator and tickets must start every call at zero
+    whatever the previous call's FFT length and sketch count: a sequence
+    mixing them on a fresh context, each against the oracle."""
     c = fcs.Context()
     seq = [([700, 600, 800], [5000, 4000, 6000], 30, 16),    # P = 16384, D = 16
            ([20, 30], [10, 12], 3, 1),                        # P = 32
