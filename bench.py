@@ -7,7 +7,13 @@ tables are generated on the device (fcs_make_hashes) and the sketches computed
 (fcs_sketch_cp).  Unit: sketches/s (one sketch = one FCS_d vector of length
 Jt, so a step yields D sketches).
 
-Other workloads (`--workload`, not the default line):
+With N = 1 the default line also carries the metric's other parts as
+sub-results under the keys `dense`, `kron` and `serve` (skip them with
+--no-extra); each has its own roofline, clock record, end-to-end leg and CPU
+baseline (serve: capacity, p50/p99 latency and an accuracy check of served
+results against direct calls).
+
+Workloads (`--workload`; the default line is `cp`):
   dense  the robust-tensor-power-method step: dense-route FCS of a symmetric
          500^3 FP32 tensor (rank 10, noise 0.01), J_n = 2000, D = 5, then
          T(u,u,u) and T(I,u,u) for 64 unit vectors with the median over D.
@@ -789,6 +795,8 @@ def run_serve(args, rank, world, local_rank):
 
     for r in reqs[:20]:
         plain(r)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
     t0 = time.perf_counter()
     ncap = min(400, nreq)
     for r in reqs[:ncap]:
@@ -856,11 +864,13 @@ def run_serve(args, rank, world, local_rank):
         th.join()
         wall = time.perf_counter() - t_start
         st = srv.stats()
-        return lat, wall, st
+        return lat, wall, st, outs
 
-    lat_srv, srv_wall, st_srv = served_run(arrivals)
-    lat_sat, sat_wall, st_sat = served_run(None)
+    lat_srv, srv_wall, st_srv, outs_srv = served_run(arrivals)
+    lat_sat, sat_wall, st_sat, _ = served_run(None)
+    clocks = sampler.stop()
     srv.close()
+    accuracy = serve_accuracy(fcs, ctx, dev, reqs, outs_srv, templates, res_shapes, resident)
     ctx.close()
     sk_total = float(sum(sk_per_req))
     plain_cap_sk = mu * sk_total / nreq
@@ -891,6 +901,8 @@ def run_serve(args, rank, world, local_rank):
             "saturation_p50_s": float(np.percentile(lat_sat, 50)),
             "saturation_p99_s": float(np.percentile(lat_sat, 99)),
         },
+        "accuracy": accuracy,
+        "clocks": clocks,
         # saturation run: per round a batched transpose + one kernel per FFT
         # size (counted by the server), per CP request a hash kernel, per
         # contraction spectrum + contract + median kernels
@@ -898,6 +910,56 @@ def run_serve(args, rank, world, local_rank):
                             + 3 * sum(1 for r in reqs if r[0] == "ct")),
     }
     return res
+
+
+def serve_accuracy(fcs, ctx, dev, reqs, outs, templates, res_shapes, resident, sample=48):
+    """Served results against direct library calls on the same inputs, for a
+    sample of the requests of the scheduled run: CP sketches in relative L2
+    per sketch (bar 1e-5); T(u,u,u) medians on the Cauchy-Schwarz scale
+    max_d ||FCS_d T|| ||FCS_d(u o u o u)|| (bar 1e-4); T(I,u,u) medians in
+    relative L2 per vector (bar 1e-4).  The served contractions read the
+    server's resident copy of each sketch, the direct ones the plain path's."""
+    import torch
+    cp_err = all_err = free_err = 0.0
+    n_cp = n_ct = 0
+    for i, r in enumerate(reqs):
+        if r[0] == "cp" and n_cp < sample:
+            I, J, R, D, U, lam = templates[r[1]]
+            h, s_ = fcs.fcs_make_hashes(ctx, r[2], I, J, D)
+            ref = fcs.fcs_sketch_cp(ctx, [torch.from_numpy(u).to(dev) for u in U],
+                                    torch.from_numpy(lam).to(dev), J, h, s_).cpu().numpy()
+            got = outs[i]
+            for d in range(D):
+                den = np.linalg.norm(ref[d]) or 1.0
+                cp_err = max(cp_err, float(np.linalg.norm(got[d] - ref[d]) / den))
+            n_cp += 1
+        elif r[0] == "ct" and n_ct < sample:
+            _, k, kind, vec = r
+            I, J, h, s_, sk = resident[k]
+            v = torch.from_numpy(vec).to(dev)
+            got = outs[i]
+            if kind == fcs.FCS_CONTRACT_ALL:
+                ref = fcs.fcs_contract(ctx, kind, sk, [v, v, v], I, J, h, s_).cpu().numpy()
+                nT = torch.linalg.norm(sk, dim=1)
+                for b in range(vec.shape[0]):
+                    ub = v[b].reshape(-1, 1).contiguous()
+                    r1 = fcs.fcs_sketch_cp(ctx, [ub, ub, ub], None, J, h, s_)
+                    scale = float((nT * torch.linalg.norm(r1, dim=1)).max())
+                    all_err = max(all_err, abs(float(got[b]) - float(ref[b])) / scale)
+            else:
+                ref = fcs.fcs_contract(ctx, kind, sk, [None, v, v], I, J, h, s_,
+                                       free_mode=0).cpu().numpy()
+                for b in range(vec.shape[0]):
+                    den = np.linalg.norm(ref[b]) or 1.0
+                    free_err = max(free_err, float(np.linalg.norm(got[b] - ref[b]) / den))
+            n_ct += 1
+        if n_cp >= sample and n_ct >= sample:
+            break
+    return {"checked_cp": n_cp, "checked_contractions": n_ct,
+            "cp_max_rel_l2": cp_err, "contract_all_max_err_cs_scale": all_err,
+            "contract_free_max_rel_l2": free_err,
+            "bars": {"cp": 1e-5, "contract_all": 1e-4, "contract_free": 1e-4},
+            "pass": cp_err <= 1e-5 and all_err <= 1e-4 and free_err <= 1e-4}
 
 
 # ================================================================== arms
@@ -950,32 +1012,41 @@ def job_rate(world, units_per_step, steps, time_ms):
     return world * units_per_step * steps / (time_ms / 1e3)
 
 
-def run_fcs(args, rank, world, local_rank):
+def measure(wname, args, rank, world, local_rank, steps, warmup, cpu_baseline=True):
+    """One workload on the FCS path: `warmup` untimed steps, then a loaded
+    clock window (the same steps, untimed, for about args.clock_window_s
+    seconds while nvidia-smi samples the clocks), then exactly `steps` timed
+    steps (CUDA events on the launching stream, L2 flushed between steps),
+    then the end-to-end leg with host buffers.  Returns the JSON dict (rank 0)."""
     import torch
     import paper_2106_13062_gb300 as fcs
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = WORKLOADS[args.workload]()
+    w = WORKLOADS[wname]()
     ctx = fcs.Context(local_rank)
     w.setup(fcs, ctx, dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    for k in range(args.warmup):
+    for k in range(warmup):
         w.step(k, lambda _: None)
     torch.cuda.synchronize()
 
     # ---- device-resident timed region: per-step events, per-kernel marks
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     marks_all = []
     sampler = ClockSampler(local_rank)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    for k in range(args.steps):
+    window = clock_window(w, flush, args.clock_window_s, warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    for k in range(steps):
         flush.zero_()                                   # L2 flush, untimed
         starts[k].record(stream)
         marks = []
@@ -984,11 +1055,12 @@ def run_fcs(args, rank, world, local_rank):
             e = torch.cuda.Event(enable_timing=True)
             e.record(stream)
             marks.append((name, e))
-        w.step(args.warmup + k, mark)
+        w.step(warmup + k, mark)
         ends[k].record(stream)
         marks_all.append(marks)
     torch.cuda.synchronize()
     clocks = sampler.stop()
+    clocks["window"] = window
     if world > 1:
         torch.distributed.barrier()
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
@@ -1001,7 +1073,7 @@ def run_fcs(args, rank, world, local_rank):
 
     # ---- end to end with host buffers (inputs H2D and results D2H per step)
     h2d, d2h = w.e2e_prepare()
-    e2e_steps = max(3, min(args.steps, 50 if args.workload != "cp" else 200))
+    e2e_steps = max(3, min(steps, 50 if wname != "cp" else 200))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(e2e_steps)]
     torch.cuda.synchronize()
@@ -1021,9 +1093,9 @@ def run_fcs(args, rank, world, local_rank):
         return None
     per_step = w.sketches_per_step()
     res = {
-        "impl": "fcs", "metric": w.metric, "value": job_rate(world, per_step, args.steps, tmax),
-        "unit": "sketches/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+        "impl": "fcs", "metric": w.metric, "value": job_rate(world, per_step, steps, tmax),
+        "unit": "sketches/s", "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": tmax / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(w.config(),
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU",
@@ -1032,15 +1104,41 @@ def run_fcs(args, rank, world, local_rank):
         "e2e": {"value": job_rate(world, per_step, 1, e2e_ms), "unit": "sketches/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms},
-        "gpu_launches": w.launches_per_step() * args.steps,
+        "gpu_launches": w.launches_per_step() * steps,
         "clocks": clocks,
         "kernel_ms": {k: statistics.mean(v) for k, v in times.items()},
     }
-    if world == 1 and not args.no_cpu_baseline:
-        v, sample = w.oracle_sample()
+    if world == 1 and cpu_baseline and not args.no_cpu_baseline:
+        v, sample = w.oracle_sample(budget_s=args.cpu_budget_s)
         res["cpu_baseline"] = {"value": v, "unit": "sketches/s", "cores": omp_threads(),
                                "kind": "oracle", "sample": sample}
     return res
+
+
+def clock_window(w, flush, seconds, k0):
+    """Untimed steps of the workload for about `seconds` (L2 flushed between
+    them, as in the timed region) so that the clock sampler sees the GPU under
+    this load; the timed steps follow directly.  Returns what ran."""
+    import torch
+    if seconds <= 0:
+        return {"steps": 0, "s": 0.0}
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        for _ in range(8):
+            flush.zero_()
+            w.step(k0 + n, lambda _: None)
+            n += 1
+        torch.cuda.synchronize()
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return {"steps": n, "s": round(time.perf_counter() - t0, 3),
+            "what": "untimed steps of this workload directly before the timed ones; "
+                    "the clock samples span them and the timed region"}
+
+
+def run_fcs(args, rank, world, local_rank):
+    return measure(args.workload, args, rank, world, local_rank, args.steps, args.warmup)
 
 
 def main():
@@ -1052,6 +1150,12 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve"], default="cp")
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload only: skip the dense, kron and serve sub-results")
+    ap.add_argument("--clock-window-s", type=float, default=1.0,
+                    help="seconds of untimed steps, sampled for clocks, before the timed ones")
+    ap.add_argument("--cpu-budget-s", type=float, default=10.0,
+                    help="seconds of CPU oracle work per cpu_baseline sample")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -1070,6 +1174,16 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     res = (run_serve if args.workload == "serve" else run_fcs)(args, rank, world, local_rank)
+    if res is not None and args.workload == "cp" and world == 1 and not args.no_extra:
+        # the metric's other parts on one GPU: the dense route and both
+        # contractions (RTPM step), Kronecker compression with recovery (HBM
+        # rooflines), and the served path against the plain one (p50/p99)
+        extra = {}
+        for name in ("dense", "kron"):
+            extra[name] = measure(name, args, rank, world, local_rank, args.steps, args.warmup)
+        extra["serve"] = run_serve(args, rank, world, local_rank)
+        res.update(extra)
+        res["extra_keys"] = sorted(extra)
     if res is not None:
         print(json.dumps(res), flush=True)
     if world > 1:

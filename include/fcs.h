@@ -25,10 +25,13 @@
  *  - Limits: 1 <= N <= 8, 1 <= D <= 16, 1 <= J_n, I_n >= 1, every entry of
  *    h for mode n in [0, J_n).  A hash value outside that range never makes
  *    a kernel touch memory out of bounds: the dense route drops the entries
- *    that use it (for that sketch only); gathers (recovery, contractions)
- *    return NaN when the summed bin leaves [0, Jt) and are otherwise
- *    unspecified.  FFT-based calls (CP route, contractions,
- *    outer combine) need Jt <= 2^20: the FFT length is P = smallest power of
+ *    that use it (for that sketch only); gathers return NaN when the bin they
+ *    read leaves their buffer -- recovery when the summed bin leaves
+ *    [0, Jt) or an index i_n leaves [0, I_n), the free-mode gather of a
+ *    contraction when h_m(i) leaves [0, P) -- and are otherwise unspecified;
+ *    the Count Sketches of a contraction's vectors drop invalid entries.
+ *    FFT-based calls (CP route, contractions, outer combine) need
+ *    Jt <= 2^20: the FFT length is P = smallest power of
  *    two >= Jt, 16 <= P <= 2^20, else FCS_EUNSUPPORTED.  P <= 16384 runs one
  *    transform per CTA in shared memory.  The CP route at P = 32768 runs one
  *    fused kernel (one 2^14-point transform per CTA in shared memory, a
@@ -36,8 +39,8 @@
  *    CTAs when the budget is small).  Other longer transforms use a two-pass
  *    FFT through the context workspace (at most min(budget, 512 MiB), work
  *    split into chunks that fit; a few MiB suffice).  fcs_sketch_cp_noalloc
- *    and the persistent batch kernel take P <= 16384 (batch plans run longer
- *    problems with their own launches).
+ *    takes P <= 16384.  Batch plans run P <= 16384 in their per-FFT-size
+ *    launch chain and longer problems with the launches above.
  *  - The library allocates only its own context workspace (device memory
  *    reused across calls, bounded by the context's budget), a 256 KiB
  *    twiddle table and, when enabled, the spectrum cache of fcs_contract.
@@ -138,7 +141,13 @@ int fcs_sketch_dense(fcs_ctx *ctx, int N, const int64_t *host_I,
  * paper's sum of inverse transforms) and one inverse FFT per sketch.
  *   host_U[N]: device pointers; U_n is I_n x R FP32 row-major with leading
  *   dimension host_ldU[n] >= R.  lambda [R] FP32 or NULL (all ones).
- *   out [D][Jt] FP32.  Needs D*(P/2+1)*8 + 64 bytes of workspace.
+ *   out [D][Jt] FP32.
+ *   Workspace for P <= 16384: A + 256 + 4*R*sum_n(I_n) bytes, rounded up to
+ *   a multiple of 256, with A = D*(P/2+2)*8 rounded up to a multiple of 256
+ *   (spectrum accumulator, tickets, factor columns transposed with lambda
+ *   folded in).  P = 32768: A + 256 + 128 KiB per CTA (fewer CTAs, down to
+ *   one, when the budget is smaller).  Longer: the two-pass route, chunked to
+ *   what the budget allows (a few MiB suffice).
  */
 int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
                   const int32_t *host_J, int64_t R, int D,
@@ -156,15 +165,22 @@ int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
  * This entry point needs no fcs_ctx and allocates nothing: its scratch is a
  * file-scope __device__ array of 4 MiB (plus a 256 KiB twiddle table) that
  * every GPU loading the library holds until the process exits.
- *   - Runs on the calling thread's current device, on `stream`.
+ *   - Runs on the calling thread's current device, on `stream`; every
+ *     pointer must be memory of that device.
  *   - The first call on a device looks up the arrays' device addresses and
  *     fills the twiddle table, synchronising `stream` once; make that first
  *     call before any stream capture.
- *   - Problems whose scratch D*(P/2+1)*8 + 512 + R*sum(I_n)*4 bytes exceed
- *     4 MiB are rejected with FCS_ENOMEM_BUDGET (nothing is launched).
+ *   - The scratch a problem needs is A + 256 + 4*R*sum_n(I_n) bytes, with
+ *     A = D*(P/2+2)*8 rounded up to a multiple of 256 (P = FFT length <=
+ *     16384).  Problems that need more than 4 MiB are rejected with
+ *     FCS_ENOMEM_BUDGET (nothing is launched); longer FFTs with
+ *     FCS_EUNSUPPORTED.
  *   - All calls share the one array: calls that overlap on the GPU (other
  *     streams, other host threads) race and corrupt each other's results.
  *     Each call clears the parts that must start at zero.
+ *   - Having no context, it cannot drop spectrum-cache entries
+ *     (fcs_cache_spectra) of `out`: after re-sketching into a buffer that a
+ *     context has cached, call fcs_forget(ctx, out) on that context.
  *   - err (may be NULL) receives a message of at most err_len bytes.
  * Arguments and output otherwise as fcs_sketch_cp.
  */
@@ -177,11 +193,16 @@ int fcs_sketch_cp_noalloc(void *stream, int N, const int64_t *host_I,
 /*
  * Batched CP-route sketches.  (The paper sketches one tensor at a time; this
  * is the batching layer over eq. (FCS_syn).)  Many CP tensors of uneven
- * order, sizes, rank and sketch length run in one persistent launch: the
- * work is cut into items (problem, sketch d, group of `grain` ranks), largest
- * FFT first, and CTAs pull items from an atomic counter; the item that
- * completes a sketch runs its inverse FFT.  Results equal fcs_sketch_cp on
- * each problem up to FP32 summation order.
+ * order, sizes, rank and sketch length run in a few launches: the work is
+ * cut into items (problem, sketch d, group of `grain` ranks) and grouped by
+ * FFT length; one batched launch transposes every problem's factor columns,
+ * then one kernel per FFT length P <= 16384 runs its items (one CTA per
+ * item, largest FFT first), the kernels chained by programmatic dependent
+ * launch so that each starts while the previous one drains.  The item that
+ * completes a sketch (a ticket counter) runs its inverse FFT.  Problems with
+ * P > 16384 follow with the long-FFT launches of fcs_sketch_cp, from
+ * plan-owned scratch.  Results equal fcs_sketch_cp on each problem up to
+ * FP32 summation order.
  */
 typedef struct fcs_cp_problem {
   int N;                    /* order, 1..8 */
@@ -210,8 +231,9 @@ int fcs_batch_plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_pr
                           int grain, fcs_batch_plan **plan);
 
 /* Issue the batch on the context's stream: one memset, one batched factor
- * transpose, one persistent kernel.  No allocation and no host
- * synchronisation, so the call may be captured into a CUDA graph. */
+ * transpose, one kernel per FFT length (the chain above) and the long
+ * problems' launches.  No allocation and no host synchronisation, so the
+ * call may be captured into a CUDA graph. */
 int fcs_batch_plan_launch(fcs_ctx *ctx, const fcs_batch_plan *plan);
 
 /* Release a plan (synchronises its context's stream first). */
@@ -332,8 +354,11 @@ int fcs_server_reset_stats(fcs_server *server);
  *  contiguous); for FREE the pointer of mode m is ignored and may be NULL.
  *  out_median: [B] (ALL) or [B][I_m] (FREE).  out_raw: NULL or [B][D] (ALL)
  *  / [B][D][I_m] (FREE).  Median over even D is the mean of the two middle
- *  values.  Needs D*(P/2+1)*8 bytes of workspace (+ the raw buffer when
- *  out_raw is NULL).
+ *  values.  Workspace: D*(P/2+1)*8 bytes for the sketch spectra (none on a
+ *  spectrum-cache hit) plus, when out_raw is NULL, 4*B*D*W bytes of raw
+ *  estimates (W = 1 for ALL, I_m for FREE), each part rounded up to a
+ *  multiple of 256.  For P > 16384 the raw buffer is a separate
+ *  context-owned allocation counted against the same budget.
  */
 int fcs_contract(fcs_ctx *ctx, int kind, int free_mode, int N,
                  const int64_t *host_I, const int32_t *host_J, int D,
@@ -370,9 +395,10 @@ int fcs_contract_both(fcs_ctx *ctx, int free_mode, int N, const int64_t *host_I,
  * least recently used evicted) and reused by later contractions with the
  * same fcsT pointer, Jt, D and FFT length, which then skip the transform of
  * the sketch (e.g. the many contractions of one RTPM or ALS loop).  The key
- * is the pointer: the library's own sketch calls drop the entries of the
- * buffers they write; after changing a cached sketch any other way, or
- * before freeing it, call fcs_forget.
+ * is the pointer: the sketch calls made through this context drop the
+ * entries of the buffers they write; after changing a cached sketch any
+ * other way (another context, fcs_sketch_cp_noalloc, a copy), or before
+ * freeing it, call fcs_forget.
  */
 int fcs_cache_spectra(fcs_ctx *ctx, int enable);
 
@@ -438,8 +464,9 @@ int fcs_als(fcs_ctx *ctx, int N, const int64_t *host_I, const int32_t *host_J, i
  * Kronecker / tensor-contraction compression subsections (its mod(., Jt) never
  * wraps and is dropped):
  *     raw[d][q] = prod_n s_n(i_n) sketch_d[sum_n h_n(i_n)],  out[q] = median_d.
- *   sketch [D][Jt]; idx [M][N] int32 multi-indices (i_n < I_n; not checked on
- *   the device).  out [M]; out_raw NULL or [D][M].  nbatch problems sharing the
+ *   sketch [D][Jt]; idx [M][N] int32 multi-indices, 0 <= i_n < I_n (checked
+ *   on the device before any load: an index outside that range gives NaN,
+ *   in out and in every raw value of that sample).  out [M]; out_raw NULL or [D][M].  nbatch problems sharing the
  *   hash tables: problem b uses sketch + b*sketch_batch_stride, idx +
  *   b*idx_batch_stride, out + b*out_batch_stride (elements; out_raw must be
  *   NULL when nbatch > 1).

@@ -243,6 +243,70 @@ def jtilde(J) -> int:
     return int(sum(int(j) for j in J) - len(J) + 1)
 
 
+def _same_device(name_tensors):
+    """Every tensor of a call must live on one device (the one the call runs on)."""
+    dev = None
+    for name, t in name_tensors:
+        if t is None:
+            continue
+        if dev is None:
+            dev = t.device
+        elif t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, expected {dev}")
+    return dev
+
+
+def _covers(h, I, name="h"):
+    """The hash tables must hold at least sum(I_n) entries per sketch row."""
+    tot = int(sum(int(i) for i in I))
+    if h.shape[1] < tot:
+        raise ValueError(f"{name} has {h.shape[1]} columns per sketch, sum(I_n) = {tot}")
+
+
+def _room(t, n: int, name: str):
+    """A caller-given output must hold at least n elements."""
+    if t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call writes {n}")
+
+
+def _check_sketch(sk, J, I, h, s, others=()):
+    """A sketch argument must be [.., D, Jt] with D matching the tables, and
+    the tables must cover every mode."""
+    if len(J) != len(I):
+        raise ValueError("need one hash length J_n per mode")
+    if sk.shape[-1] != jtilde(J):
+        raise ValueError(f"sketch rows hold {sk.shape[-1]} bins, Jt = {jtilde(J)}")
+    if sk.dim() < 2 or sk.shape[-2] > h.shape[0]:
+        raise ValueError("sketch must be [.., D, Jt] with at least D rows of hash tables")
+    _covers(h, I)
+    _same_device([("sketch", sk), ("h", h), ("s", s),
+                  *[(f"argument {k}", t) for k, t in enumerate(others)]])
+
+
+def _check_cp(U, lam, J, h, s, out):
+    """Shape checks shared by the CP-route wrappers: factors I_n x R with unit
+    column stride, one hash length per mode, lambda of at least R entries,
+    tables covering every mode, and room for D x Jt outputs."""
+    N = len(U)
+    if N < 1 or len(J) != N:
+        raise ValueError("need one hash length J_n per factor matrix")
+    R = U[0].shape[1]
+    for k, u in enumerate(U):
+        _need(u, torch.float32, f"U[{k}]", contiguous=False)
+        if u.dim() != 2 or u.shape[1] != R or u.stride(1) != 1:
+            raise ValueError("each U_n must be I_n x R with unit column stride")
+    if lam is not None:
+        _need(lam, torch.float32, "lambda")
+        _room(lam, R, "lambda")
+    _covers(h, [u.shape[0] for u in U])
+    if out is not None:
+        _need(out, torch.float32, "out")
+        _room(out, h.shape[0] * jtilde(J), "out")
+    _same_device([("U[0]", U[0]), *[(f"U[{k}]", u) for k, u in enumerate(U)],
+                  ("lambda", lam), ("h", h), ("s", s), ("out", out)])
+    return N, R
+
+
 class Context:
     """An fcs_ctx bound to one device and (by default) torch's current
     stream of that device at each call."""
@@ -320,10 +384,13 @@ def fcs_sketch_dense(ctx: Context, T: torch.Tensor, J, h, s, ldh: int = 0,
     nb = T.shape[0] if batched else 1
     if len(shape) != len(J):
         raise ValueError("T's order does not match len(J)")
+    _covers(h, shape)
     if out is None:
         out = torch.empty(((nb,) if batched else ()) + (D, Jt),
                           dtype=torch.float32, device=T.device)
     _need(out, torch.float32, "out")
+    _room(out, nb * D * Jt, "out")
+    _same_device([("T", T), ("h", h), ("s", s), ("out", out)])
     ctx.check(lib().fcs_sketch_dense(
         ctx.handle, len(J), _arr(C.c_int64, shape), _arr(C.c_int64, strides),
         _arr(C.c_int32, J), D, _ptr(T), _ptr(h), _ptr(s), ldh, _ptr(out), nb,
@@ -337,19 +404,11 @@ def fcs_sketch_cp(ctx: Context, U, lam, J, h, s, ldh: int = 0,
     row-major).  Returns [D, Jt]."""
     ctx._sync_stream()
     ldh = _tables(h, s, ldh)
-    N = len(U)
-    R = U[0].shape[1]
-    for k, u in enumerate(U):
-        _need(u, torch.float32, f"U[{k}]", contiguous=False)
-        if u.dim() != 2 or u.shape[1] != R or u.stride(1) != 1:
-            raise ValueError("each U_n must be I_n x R with unit column stride")
-    if lam is not None:
-        _need(lam, torch.float32, "lambda")
+    N, R = _check_cp(U, lam, J, h, s, out)
     D = h.shape[0]
     Jt = jtilde(J)
     if out is None:
         out = torch.empty((D, Jt), dtype=torch.float32, device=U[0].device)
-    _need(out, torch.float32, "out")
     ptrs = (C.c_void_p * N)(*[u.data_ptr() for u in U])
     ctx.check(lib().fcs_sketch_cp(
         ctx.handle, N, _arr(C.c_int64, [u.shape[0] for u in U]),
@@ -362,28 +421,25 @@ def fcs_sketch_cp_noalloc(U, lam, J, h, s, ldh: int = 0,
                           out: torch.Tensor | None = None):
     """fcs_sketch_cp without a context and without device allocation inside
     the library (scratch lives in a fixed 4 MiB device array; see
-    include/fcs.h).  Runs on torch's current device and stream.  The output
-    tensor is allocated here by torch unless `out` is given."""
+    include/fcs.h).  Runs on the device that holds the tensors (made current
+    for the call) and on torch's current stream of that device.  The output
+    tensor is allocated here by torch unless `out` is given.  This call does
+    not drop spectrum-cache entries of `out` in any context: call fcs_forget
+    on each caching context after re-sketching into a cached buffer."""
     ldh = _tables(h, s, ldh)
-    N = len(U)
-    R = U[0].shape[1]
-    for k, u in enumerate(U):
-        _need(u, torch.float32, f"U[{k}]", contiguous=False)
-        if u.dim() != 2 or u.shape[1] != R or u.stride(1) != 1:
-            raise ValueError("each U_n must be I_n x R with unit column stride")
-    if lam is not None:
-        _need(lam, torch.float32, "lambda")
+    N, R = _check_cp(U, lam, J, h, s, out)
     D = h.shape[0]
+    dev = U[0].device
     if out is None:
-        out = torch.empty((D, jtilde(J)), dtype=torch.float32, device=U[0].device)
-    _need(out, torch.float32, "out")
+        out = torch.empty((D, jtilde(J)), dtype=torch.float32, device=dev)
     ptrs = (C.c_void_p * N)(*[u.data_ptr() for u in U])
     err = C.create_string_buffer(256)
-    stream = torch.cuda.current_stream(U[0].device).cuda_stream
-    rc = lib().fcs_sketch_cp_noalloc(
-        C.c_void_p(stream), N, _arr(C.c_int64, [u.shape[0] for u in U]),
-        _arr(C.c_int32, J), R, D, ptrs, _arr(C.c_int64, [u.stride(0) for u in U]),
-        _ptr(lam), _ptr(h), _ptr(s), ldh, _ptr(out), err, 256)
+    with torch.cuda.device(dev):
+        stream = torch.cuda.current_stream(dev).cuda_stream
+        rc = lib().fcs_sketch_cp_noalloc(
+            C.c_void_p(stream), N, _arr(C.c_int64, [u.shape[0] for u in U]),
+            _arr(C.c_int32, J), R, D, ptrs, _arr(C.c_int64, [u.stride(0) for u in U]),
+            _ptr(lam), _ptr(h), _ptr(s), ldh, _ptr(out), err, 256)
     if rc != FCS_OK:
         raise FcsError(rc, err.value.decode(errors="replace"))
     return out
@@ -427,6 +483,7 @@ def fcs_contract(ctx: Context, kind: int, fcsT: torch.Tensor, vecs, I, J, h, s,
         ptrs[n] = v.data_ptr()
     if B is None:
         raise ValueError("no vectors given")
+    _check_sketch(fcsT, J, I, h, s, [v for v in vecs if v is not None])
     dev = fcsT.device
     if kind == FCS_CONTRACT_ALL:
         med = torch.empty((B,), dtype=torch.float32, device=dev)
@@ -462,6 +519,7 @@ def fcs_contract_both(ctx: Context, fcsT: torch.Tensor, vecs, I, J, h, s,
         if v.shape != (B, int(I[n])):
             raise ValueError(f"vecs[{n}] must be [B, I_{n}]")
         ptrs[n] = v.data_ptr()
+    _check_sketch(fcsT, J, I, h, s, vecs)
     dev = fcsT.device
     Im = int(I[free_mode])
     med_all = torch.empty((B,), dtype=torch.float32, device=dev)
@@ -492,6 +550,9 @@ def fcs_recover(ctx: Context, sketch: torch.Tensor, I, J, h, s, idx: torch.Tenso
     M = idx.shape[-2]
     if idx.shape[-1] != N:
         raise ValueError("idx must be [.., M, N]")
+    if batched != (idx.dim() == 3) or (batched and idx.shape[0] != nb):
+        raise ValueError("batched sketch [B, D, Jt] needs idx [B, M, N]")
+    _check_sketch(sketch, J, I, h, s, [idx])
     out = torch.empty(((nb,) if batched else ()) + (M,), dtype=torch.float32,
                       device=sketch.device)
     rawt = None
@@ -588,6 +649,7 @@ def fcs_rtpm(ctx: Context, fcsT: torch.Tensor, I: int, J, h, s, init: torch.Tens
     K, L, Ii = init.shape
     if Ii != int(I):
         raise ValueError("init must be [K, L, I]")
+    _check_sketch(fcsT, J, [int(I)] * len(J), h, s, [init])
     lam = torch.empty(K, dtype=torch.float32, device=fcsT.device)
     U = torch.empty((K, Ii), dtype=torch.float32, device=fcsT.device)
     ctx.check(lib().fcs_rtpm(ctx.handle, len(J), int(I), _arr(C.c_int32, J), fcsT.shape[0],
@@ -605,6 +667,9 @@ def fcs_als(ctx: Context, fcsT: torch.Tensor, I, J, h, s, F, n_iter: int, ldh: i
     for n, f in enumerate(F):
         _need(f, torch.float32, f"F[{n}]")
     R = F[0].shape[0]
+    if len(F) != len(I) or any(f.dim() != 2 or f.shape != (R, int(i)) for f, i in zip(F, I)):
+        raise ValueError("F must hold one [R, I_n] tensor per mode")
+    _check_sketch(fcsT, J, I, h, s, F)
     lam = torch.empty(R, dtype=torch.float32, device=fcsT.device)
     fp = (C.c_void_p * len(F))(*[f.data_ptr() for f in F])
     ctx.check(lib().fcs_als(ctx.handle, len(I), _arr(C.c_int64, I), _arr(C.c_int32, J),
@@ -620,20 +685,12 @@ def cp_problem(U, lam, J, h, s, ldh: int = 0, out: torch.Tensor | None = None):
     unless given).  The caller keeps U, lam, h, s and out alive while any
     plan built from the description may run."""
     ldh = _tables(h, s, ldh)
-    N = len(U)
-    if N > 8:
+    if len(U) > 8:
         raise ValueError("order > 8")
-    R = U[0].shape[1]
-    for k, u in enumerate(U):
-        _need(u, torch.float32, f"U[{k}]", contiguous=False)
-        if u.dim() != 2 or u.shape[1] != R or u.stride(1) != 1:
-            raise ValueError("each U_n must be I_n x R with unit column stride")
-    if lam is not None:
-        _need(lam, torch.float32, "lambda")
+    N, R = _check_cp(U, lam, J, h, s, out)
     D = h.shape[0]
     if out is None:
         out = torch.empty((D, jtilde(J)), dtype=torch.float32, device=U[0].device)
-    _need(out, torch.float32, "out")
     pr = CpProblem()
     pr.N, pr.D, pr.R = N, D, R
     for k in range(N):

@@ -413,9 +413,10 @@ extern "C" int fcs_sketch_cp_noalloc(void *stream, int N, const int64_t *host_I,
   if (err && err_len) err[0] = '\0';
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CpArgs a{};
-  if (make_modes(nullptr, N, host_I, host_J, ldh, &a.m) != FCS_OK)
-    return noalloc_fail(err, err_len, FCS_EINVAL,
-                        "invalid N, I_n, J_n or ldh (1 <= N <= %d, I_n >= 1, J_n >= 1)", kMaxN);
+  {
+    const int mrc = make_modes_msg(err, err_len, N, host_I, host_J, ldh, &a.m);
+    if (mrc != FCS_OK) return mrc;
+  }
   if (D < 1 || D > kMaxD)
     return noalloc_fail(err, err_len, FCS_EINVAL, "D=%d outside [1,%d]", D, kMaxD);
   if (R < 1) return noalloc_fail(err, err_len, FCS_EINVAL, "R=%lld must be >= 1", (long long)R);

@@ -76,18 +76,30 @@ int ensure_raw(fcs_ctx *ctx, size_t bytes) {
   return FCS_OK;
 }
 
-int make_modes(fcs_ctx *ctx, int N, const int64_t *host_I, const int32_t *host_J,
-               int64_t ldh, Modes *m) {
-  if (N < 1 || N > kMaxN) return set_error(ctx, FCS_EINVAL, "N=%d outside [1,%d]", N, kMaxN);
-  if (!host_I || !host_J) return set_error(ctx, FCS_EINVAL, "host_I/host_J is NULL");
+namespace {
+int msg_fail(char *err, size_t n, int code, const char *fmt, ...) {
+  if (err && n) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(err, n, fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+}  // namespace
+
+int make_modes_msg(char *err, size_t errn, int N, const int64_t *host_I,
+                   const int32_t *host_J, int64_t ldh, Modes *m) {
+  if (N < 1 || N > kMaxN) return msg_fail(err, errn, FCS_EINVAL, "N=%d outside [1,%d]", N, kMaxN);
+  if (!host_I || !host_J) return msg_fail(err, errn, FCS_EINVAL, "host_I/host_J is NULL");
   m->N = N;
   int64_t tot = 0, jt = 1;
   for (int n = 0; n < N; ++n) {
     if (host_I[n] < 1 || host_I[n] > (int64_t(1) << 31) - 1)
-      return set_error(ctx, FCS_EINVAL, "I[%d]=%lld outside [1, 2^31)", n,
-                       (long long)host_I[n]);
+      return msg_fail(err, errn, FCS_EINVAL, "I[%d]=%lld outside [1, 2^31)", n,
+                      (long long)host_I[n]);
     if (host_J[n] < 1)
-      return set_error(ctx, FCS_EINVAL, "J[%d]=%d must be >= 1", n, host_J[n]);
+      return msg_fail(err, errn, FCS_EINVAL, "J[%d]=%d must be >= 1", n, host_J[n]);
     m->I[n] = host_I[n];
     m->J[n] = host_J[n];
     m->off[n] = tot;
@@ -101,12 +113,21 @@ int make_modes(fcs_ctx *ctx, int N, const int64_t *host_I, const int32_t *host_J
   }
   if (ldh == 0) ldh = tot;
   if (ldh < tot)
-    return set_error(ctx, FCS_EINVAL, "ldh=%lld smaller than sum(I)=%lld",
-                     (long long)ldh, (long long)tot);
+    return msg_fail(err, errn, FCS_EINVAL, "ldh=%lld smaller than sum(I)=%lld",
+                    (long long)ldh, (long long)tot);
   if (jt > (int64_t(1) << 30))
-    return set_error(ctx, FCS_EUNSUPPORTED, "sketch length %lld too large", (long long)jt);
+    return msg_fail(err, errn, FCS_EUNSUPPORTED, "sketch length %lld too large", (long long)jt);
   m->ldh = ldh;
   m->Jt = jt;
+  return FCS_OK;
+}
+
+int make_modes(fcs_ctx *ctx, int N, const int64_t *host_I, const int32_t *host_J,
+               int64_t ldh, Modes *m) {
+  char buf[256];
+  buf[0] = '\0';
+  const int rc = make_modes_msg(buf, sizeof(buf), N, host_I, host_J, ldh, m);
+  if (rc) return set_error(ctx, rc, "%s", buf);
   return FCS_OK;
 }
 

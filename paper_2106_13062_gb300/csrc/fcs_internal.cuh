@@ -485,6 +485,9 @@ struct Modes {
 
 int make_modes(fcs_ctx *ctx, int N, const int64_t *host_I, const int32_t *host_J,
                int64_t ldh, Modes *m);
+// make_modes without a context: the message goes to err (n bytes, may be NULL).
+int make_modes_msg(char *err, size_t n, int N, const int64_t *host_I,
+                   const int32_t *host_J, int64_t ldh, Modes *m);
 
 // FFT-based calls for kMaxLog2P < log2p <= kMaxLog2PBig (fcs_big.cu); the
 // callers have validated the arguments.

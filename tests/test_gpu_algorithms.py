@@ -169,3 +169,96 @@ def test_als_matches_oracle(fcs, ctx, orc, alg):
     # the same); the tighter quality pin is the oracle's own test
     That = np.einsum("r,ri,rj,rk->ijk", lam, *[host(f) for f in F])
     assert np.linalg.norm(That - T) / np.linalg.norm(T) <= 0.25
+
+
+# Loop tolerances.  Each GPU contraction is within the contraction bar
+# (1e-4 on its own scale; about 1e-6 observed) of the FP64 contraction of the
+# same sketch.  A power iteration near a fixed point of an orthogonal tensor
+# converges quadratically, so a perturbation of size e in one step leaves
+# O(e) in the final vector and eigenvalue rather than growing: the RTPM loops
+# are compared at 1e-3.  One ALS update solves with G = *_{n != m} F_n F_n^T,
+# which multiplies a relative error of the columns by at most cond(G); the
+# ALS loops are compared at 1e-3 * max(1, sweeps * N * cond(G) * 1e-2) on the
+# factors, with cond(G) taken from the oracle's final factors.
+
+def test_rtpm_paper_size(fcs, ctx, orc, alg):
+    """Sketched RTPM on the synthetic 100^3 symmetric tensor of the RTPM
+    experiments (rank 10, weights 10..1, noise 0.01), J_n = 3000 (Jt = 8998,
+    P = 16384), D = 3: the GPU loop equals the oracle's loop from the same
+    starts; the three leading components are recovered; the residual norm
+    ||T - sum_k lambda_k u_k o u_k o u_k|| / ||T|| is reported."""
+    I, J, D = 100, [3000] * 3, 3
+    T, V, w = synth.rtpm_tensor(71, I=I, R=10, sigma=0.01)
+    ho, so = orc.make_hashes(72, [I] * 3, J, D)
+    hg, sg = cuda(ho), cuda(so)
+    Tg = cuda(T)
+    fT = fcs.fcs_sketch_dense(ctx, Tg, J, hg, sg)
+    K, L, it = 3, 5, 8
+    init = np.random.default_rng(73).standard_normal((K, L, I)).astype(np.float32)
+    lam, U = fcs.fcs_rtpm(ctx, fT, I, J, hg, sg, cuda(init), it)
+    lam, U = host(lam), host(U)
+    lref, Uref = alg.rtpm(host(fT).astype(np.float64), 3, I, J, ho, so, K, L, it, init)
+    np.testing.assert_allclose(lam, lref, rtol=1e-3)
+    np.testing.assert_allclose(U, Uref, atol=1e-3)
+    Ug = torch.from_numpy(U).cuda().double()
+    That = torch.einsum("k,ki,kj,kl->ijl", torch.from_numpy(lam).cuda().double(), Ug, Ug, Ug)
+    res = float(torch.linalg.norm(Tg.double() - That) / torch.linalg.norm(Tg.double()))
+    Vg = torch.from_numpy(V[:, :K].T.copy()).cuda()
+    best = torch.einsum("k,ki,kj,kl->ijl", torch.from_numpy(w[:K]).cuda(), Vg, Vg, Vg)
+    res_best = float(torch.linalg.norm(Tg.double() - best) / torch.linalg.norm(Tg.double()))
+    # each recovered vector matched to the true component it aligns with
+    match = np.abs(U @ V).argmax(axis=1)
+    align = np.abs(U @ V)[np.arange(K), match]
+    print(f"\nRTPM 100^3 J=3000 D=3 K=3: lambda={lam.round(4).tolist()} matched weights="
+          f"{w[match].tolist()} |<u,v>|={align.round(4).tolist()} residual={res:.4f} "
+          f"(true top-3 components: {res_best:.4f})")
+    assert len(set(match.tolist())) == K and set(match.tolist()) <= {0, 1, 2, 3}
+    assert (align >= 0.95).all()
+    np.testing.assert_allclose(lam, w[match], rtol=0.2)
+    assert res <= res_best + 0.05
+
+
+@pytest.mark.parametrize("Jn", [3000, 7000])
+def test_als_paper_size(fcs, ctx, orc, alg, Jn):
+    """Sketched CP-ALS on a 400^3 rank-10 CP tensor (the ALS experiments'
+    largest synthetic size), J_n = 3000 (P = 16384) and 7000 (Jt = 20998,
+    P = 32768: the two-pass contraction route), D = 3, three sweeps from
+    the true factors plus 0.3 N(0,1) noise: the GPU loop equals the oracle's
+    loop; the residual ||T - T_hat|| / ||T|| is reported."""
+    I, R, D, sweeps = [400] * 3, 10, 3, 3
+    J = [Jn] * 3
+    Uf, lamt = synth.cp_factors(81, I, R)
+    Tg = torch.einsum("r,ir,jr,kr->ijk", *[torch.from_numpy(x).cuda().double()
+                                           for x in (lamt, *Uf)]).float()
+    ho, so = orc.make_hashes(82, I, J, D)
+    hg, sg = cuda(ho), cuda(so)
+    fT = fcs.fcs_sketch_dense(ctx, Tg, J, hg, sg)
+    g = np.random.default_rng(83)
+    init = [(u.T + 0.3 * g.standard_normal((R, i))).astype(np.float32) for u, i in zip(Uf, I)]
+    F = [cuda(x.copy()) for x in init]
+    lam = host(fcs.fcs_als(ctx, fT, I, J, hg, sg, F, sweeps))
+    Fref, lref = alg.als(host(fT).astype(np.float64), I, J, ho, so, R, sweeps, init)
+    G = np.ones((R, R))
+    for f in Fref[1:]:
+        G *= f @ f.T
+    tol = 1e-3 * max(1.0, sweeps * 3 * np.linalg.cond(G) * 1e-2)
+    np.testing.assert_allclose(lam, lref, rtol=tol)
+    for f, fr in zip(F, Fref):
+        np.testing.assert_allclose(host(f), fr, atol=tol)
+    def residual(lam_, F_):
+        Fd = [torch.as_tensor(np.asarray(f, dtype=np.float64)).cuda() for f in F_]
+        That = torch.einsum("r,ri,rj,rk->ijk", torch.as_tensor(np.asarray(lam_, np.float64)).cuda(),
+                            *Fd)
+        return float(torch.linalg.norm(Tg.double() - That) / torch.linalg.norm(Tg.double()))
+    res = residual(lam, [host(f) for f in F])
+    res_orc = residual(lref, Fref)
+    # the starting point's residual, with its least-squares weights
+    X = [x / np.linalg.norm(x, axis=1, keepdims=True) for x in init]
+    Tn = Tg.double()
+    Xd = [torch.from_numpy(x.astype(np.float64)).cuda() for x in X]
+    Kr = torch.einsum("ri,rj,rk->rijk", *Xd).reshape(R, -1)
+    l0 = torch.linalg.lstsq(Kr.T, Tn.reshape(-1, 1)).solution.reshape(-1).cpu().numpy()
+    res0 = residual(l0, X)
+    print(f"\nALS 400^3 rank 10 J={Jn} D=3, {sweeps} sweeps from the true factors + 0.3 N(0,1): "
+          f"residual start {res0:.4f} -> GPU {res:.4f} (oracle loop {res_orc:.4f})")
+    assert abs(res - res_orc) <= 10 * tol * max(1.0, res_orc)

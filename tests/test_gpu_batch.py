@@ -1,4 +1,5 @@
-"""Batched CP-route sketches: one persistent launch over problems of uneven
+"""Batched CP-route sketches: a plan (one transpose launch, then one kernel per
+FFT length, chained by programmatic dependent launch) over problems of uneven
 order, sizes, rank and sketch length must give each problem's fcs_sketch_cp
 result (and the oracle's) within the sketch tolerance.  Needs a GPU."""
 from __future__ import annotations

@@ -103,11 +103,42 @@ def test_result_same_alone_and_in_mix(fcs):
     srv.close()
 
 
-def test_contractions_on_resident_sketch(fcs, ctx):
+def _contract_refs(orc, sk, I, J, ho, so, u, m=0):
+    """FP64 oracle contractions of the (FP32) sketch sk with u in every mode:
+    per-sketch T(u,u,u) and its Cauchy-Schwarz scale ||FCS_d T|| ||FCS_d(u o u o u)||,
+    and per-sketch T(I,u,u) with free mode m."""
+    fT = sk.astype(np.float64)
+    B, D = u.shape[0], sk.shape[0]
+    ref, scale = np.zeros((B, D)), np.zeros((B, D))
+    refs = np.zeros((B, D, I[m]))
+    for b in range(B):
+        vb = [u[b].astype(np.float64)] * len(I)
+        ref[b] = orc.contract_all(fT, vb, J, ho, so)
+        r1 = orc.fcs_cp([x[:, None] for x in vb], None, J, ho, so)
+        scale[b] = np.linalg.norm(fT, axis=1) * np.linalg.norm(r1, axis=1)
+        refs[b] = orc.contract_free(fT, vb, m, J, ho, so)
+    return ref, scale, refs
+
+
+def _assert_contract_close(orc, r_all, r_free, ref, scale, refs):
+    """Medians within the contraction bar of the oracle's medians: T(u,u,u) on
+    the Cauchy-Schwarz scale, T(I,u,u) in relative L2 of the largest sketch."""
+    merr = np.abs(r_all - orc.median(ref.T)) / scale.max(axis=1)
+    assert merr.max() <= CONTRACT_RTOL, f"T(u,u,u) median error {merr.max():.3e}"
+    for b in range(refs.shape[0]):
+        e = np.linalg.norm(r_free[b] - orc.median(refs[b]))
+        assert e <= CONTRACT_RTOL * np.linalg.norm(refs[b], axis=1).max()
+
+
+def test_contractions_on_resident_sketch(fcs, ctx, orc):
+    """Served T(u,u,u) and T(I,u,u) against a resident sketch equal the
+    oracle's contractions of that same sketch (copied out by the request that
+    made it resident) and the direct library calls, at the contraction bar."""
     I, J, R, D, B = [60, 60, 60], [300, 300, 300], 8, 5, 7
     U, lam = synth.cp_factors(9, I, R)
     srv = fcs.FcsServer(streams=2)
-    t = srv.submit_cp(U, lam, J, D, seed=91, keep_resident=True)
+    sk = np.zeros((D, sum(J) - 2), dtype=np.float32)
+    t = srv.submit_cp(U, lam, J, D, seed=91, out=sk, keep_resident=True)
     res = srv.wait(t, 60.0)
     assert res.state == 2 and res.sketch_id > 0
     sid = res.sketch_id
@@ -117,18 +148,73 @@ def test_contractions_on_resident_sketch(fcs, ctx):
     t1 = srv.submit_contract(sid, I, J, fcs.FCS_CONTRACT_ALL, [u, u, u], r_all)
     t2 = srv.submit_contract(sid, I, J, fcs.FCS_CONTRACT_FREE, [None, u, u], r_free)
     assert srv.wait(t1, 60.0).state == 2 and srv.wait(t2, 60.0).state == 2
-    sk, h, s = _direct(fcs, ctx, U, lam, J, D, 91)
-    ug = cuda(u)
-    a = host(fcs.fcs_contract(ctx, fcs.FCS_CONTRACT_ALL, cuda(sk), [ug] * 3, I, J, h, s))
+    ho, so = orc.make_hashes(91, I, J, D)
+    ref, scale, refs = _contract_refs(orc, sk, I, J, ho, so, u)
+    _assert_contract_close(orc, r_all, r_free, ref, scale, refs)
+    # the direct library calls on the same sketch
+    ug, hg, sg = cuda(u), cuda(ho), cuda(so)
+    a = host(fcs.fcs_contract(ctx, fcs.FCS_CONTRACT_ALL, cuda(sk), [ug] * 3, I, J, hg, sg))
     b = host(fcs.fcs_contract(ctx, fcs.FCS_CONTRACT_FREE, cuda(sk), [None, ug, ug], I, J,
-                              h, s, free_mode=0))
-    scale = np.abs(a).max() + 1e-30
-    assert np.abs(r_all - a).max() <= 1e-3 * scale
-    assert rel_l2(r_free, b) <= 1e-3
+                              hg, sg, free_mode=0))
+    assert (np.abs(r_all - a) / scale.max(axis=1)).max() <= CONTRACT_RTOL
+    for k in range(B):
+        assert np.linalg.norm(r_free[k] - b[k]) <= CONTRACT_RTOL * np.linalg.norm(refs[k], axis=1).max()
     assert srv.release(sid) == 0
     with pytest.raises(fcs.FcsError) as e:        # released sketches are gone
         srv.submit_contract(sid, I, J, fcs.FCS_CONTRACT_ALL, [u, u, u], r_all)
     assert e.value.code == fcs.FCS_EINVAL
+    srv.close()
+
+
+def test_contractions_same_alone_and_in_mix(fcs, orc):
+    """Both contraction kinds against a resident sketch give the same result
+    when served alone on an idle server and when submitted in the middle of a
+    burst of CP sketch requests from two threads (rounds overlapping on the
+    device), within the contraction bar; both equal the oracle's."""
+    I, J, R, D, B = [120, 120, 120], [900, 900, 900], 12, 6, 9
+    U, lam = synth.cp_factors(21, I, R)
+    srv = fcs.FcsServer(streams=4, max_inflight=48, max_batch=16)
+    sk = np.zeros((D, sum(J) - 2), dtype=np.float32)
+    res = srv.wait(srv.submit_cp(U, lam, J, D, seed=22, out=sk, keep_resident=True), 60.0)
+    assert res.state == 2
+    sid = res.sketch_id
+    u = synth.unit_vectors(23, B, 120)
+
+    def submit_both():
+        ra = np.zeros(B, dtype=np.float32)
+        rf = np.zeros((B, 120), dtype=np.float32)
+        ta = srv.submit_contract(sid, I, J, fcs.FCS_CONTRACT_ALL, [u, u, u], ra)
+        tf = srv.submit_contract(sid, I, J, fcs.FCS_CONTRACT_FREE, [None, u, u], rf)
+        return ta, tf, ra, rf
+
+    ta, tf, alone_a, alone_f = submit_both()
+    assert srv.wait(ta, 60.0).state == 2 and srv.wait(tf, 60.0).state == 2
+    tickets = []
+
+    def burst(seed0):
+        gg = np.random.default_rng(seed0)
+        for k in range(20):
+            I2, J2, R2, D2 = _shape(gg)
+            U2, l2 = synth.cp_factors(seed0 * 100 + k, I2, R2)
+            o2 = np.zeros((D2, sum(J2) - len(J2) + 1), dtype=np.float32)
+            tickets.append(srv.submit_cp(U2, l2, J2, D2, seed=k, out=o2))
+    th = threading.Thread(target=burst, args=(5,))
+    th.start()
+    ta, tf, mix_a, mix_f = submit_both()
+    burst(6)
+    th.join()
+    assert srv.wait(ta, 60.0).state == 2 and srv.wait(tf, 60.0).state == 2
+    for t in tickets:
+        assert srv.wait(t, 60.0).state == 2
+    assert srv.stats().max_inflight_seen > 1       # it really ran in a mix
+    ho, so = orc.make_hashes(22, I, J, D)
+    ref, scale, refs = _contract_refs(orc, sk, I, J, ho, so, u)
+    assert (np.abs(mix_a - alone_a) / scale.max(axis=1)).max() <= CONTRACT_RTOL
+    for k in range(B):
+        assert np.linalg.norm(mix_f[k] - alone_f[k]) <= \
+            CONTRACT_RTOL * np.linalg.norm(refs[k], axis=1).max()
+    _assert_contract_close(orc, alone_a, alone_f, ref, scale, refs)
+    _assert_contract_close(orc, mix_a, mix_f, ref, scale, refs)
     srv.close()
 
 

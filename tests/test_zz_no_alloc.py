@@ -71,3 +71,36 @@ def test_noalloc_rejects_oversized_problem():
     rc, msg = _call_noalloc(fcs, U, None, J, h, s, out)
     assert rc == fcs.FCS_ENOMEM_BUDGET
     assert "scratch" in msg
+
+
+def test_noalloc_wrapper_and_spectrum_cache(orc):
+    """Through the Python wrapper: the result equals fcs_sketch_cp's; a buffer
+    re-sketched by the no-alloc call while a context caches its spectra is
+    read correctly by later contractions once fcs_forget has dropped the
+    entry (the entry point has no context, so it cannot drop it itself)."""
+    import paper_2106_13062_gb300 as fcs
+    fcs.build()
+    ctx = fcs.Context()
+    fcs.fcs_cache_spectra(ctx, True)
+    I, J, R, D = [120, 90, 70], [300, 250, 200], 6, 3
+    h, s = fcs.fcs_make_hashes(ctx, 41, I, J, D)
+    Ua, lama = synth.cp_factors(42, I, R)
+    Ub, lamb = synth.cp_factors(43, I, R)
+    cu = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    buf = fcs.fcs_sketch_cp(ctx, [cu(u) for u in Ua], cu(lama), J, h, s)
+    v = [cu(synth.unit_vectors(44 + n, 2, I[n])) for n in range(3)]
+    vecs = [None, v[1], v[2]]
+    fcs.fcs_contract(ctx, fcs.FCS_CONTRACT_FREE, buf, vecs, I, J, h, s)   # caches buf
+    ref = fcs.fcs_sketch_cp(ctx, [cu(u) for u in Ub], cu(lamb), J, h, s)
+    fcs.fcs_sketch_cp_noalloc([cu(u) for u in Ub], cu(lamb), J, h, s, out=buf)
+    torch.cuda.synchronize()
+    for d in range(D):
+        assert rel_l2(buf[d].cpu().numpy(), ref[d].cpu().numpy()) <= SKETCH_RTOL
+    fcs.fcs_forget(ctx, buf)
+    got = fcs.fcs_contract(ctx, fcs.FCS_CONTRACT_FREE, buf, vecs, I, J, h, s)
+    want = fcs.fcs_contract(ctx, fcs.FCS_CONTRACT_FREE, buf.clone(), vecs, I, J, h, s)
+    torch.cuda.synchronize()
+    assert rel_l2(got.cpu().numpy(), want.cpu().numpy()) <= 1e-6
+    with pytest.raises(ValueError):
+        fcs.fcs_sketch_cp_noalloc([cu(u) for u in Ub], cu(lamb), J, h, s, out=buf[:, :-1])
+    ctx.close()
