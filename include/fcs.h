@@ -87,7 +87,10 @@ int fcs_create(fcs_ctx **ctx, int device, void *stream, size_t mem_budget_bytes)
  * stream first).  NULL is accepted. */
 int fcs_destroy(fcs_ctx *ctx);
 
-/* Change the stream later calls are issued on. */
+/* Change the stream later calls are issued on.  The new stream is made to
+ * wait (an event, no host synchronisation) for the work already queued on
+ * the old one, since both use the context's buffers; while either stream is
+ * being captured into a CUDA graph the switch is made without that wait. */
 int fcs_set_stream(fcs_ctx *ctx, void *stream);
 
 /* Message for the last failing call on this context ("" if none).  The
@@ -225,7 +228,8 @@ typedef struct fcs_batch_plan fcs_batch_plan;
  * device memory (counted against the context budget).  grain = ranks per
  * item; 0 = the autotuned grain for this batch shape if fcs_batch_autotune
  * has seen it (this context or the FCS_AUTOTUNE_CACHE file), else a default
- * of about four items per SM.  The plan records the problems' device
+ * of about four items per SM.  The class shapes are the autotuned ones for
+ * this batch shape when known, else the defaults.  The plan records the problems' device
  * pointers: later launches read whatever those buffers hold then. */
 int fcs_batch_plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
                           int grain, fcs_batch_plan **plan);
@@ -243,11 +247,37 @@ int fcs_batch_plan_destroy(fcs_batch_plan *plan);
 int fcs_batch_sketch_cp(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
                         int grain);
 
-/* Autotuner: time the whole batch on the device for grains 1, 2, 4, ...
- * (up to 64 and 2R), keep the fastest for this batch shape (sorted
- * (FFT length, N, D, R, max I_n) of every problem), write it to
- * *host_best_grain and, when the environment variable FCS_AUTOTUNE_CACHE
- * names a file, persist the table there. */
+/* Shape of one FFT-length class of a batch plan.  thread_mult: 1 = one
+ * radix-16 butterfly per thread (P/32 threads, at least 32), 2 = twice as
+ * many threads (P <= 8192 only).  items_per_cta: 1, 2 or 4 work items run one
+ * after another by each CTA.  threads: the block size that results (output
+ * of fcs_batch_plan_config, ignored on input). */
+typedef struct fcs_batch_class_cfg {
+  int fft_len;              /* P, a power of two in [16, 16384] */
+  int thread_mult;
+  int items_per_cta;
+  int threads;
+} fcs_batch_class_cfg;
+
+/* fcs_batch_plan_create with explicit class shapes (classes not listed take
+ * thread_mult = 1, items_per_cta = 1) and grain (0 = the default grain). */
+int fcs_batch_plan_create_cfg(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
+                              int grain, int ncfg, const fcs_batch_class_cfg *host_cfg,
+                              fcs_batch_plan **plan);
+
+/* The grain and class shapes a plan was built with: *host_ncfg classes (the
+ * first max_cfg of them copied to host_cfg, largest FFT first). */
+int fcs_batch_plan_config(const fcs_batch_plan *plan, int *host_grain, int max_cfg,
+                          fcs_batch_class_cfg *host_cfg, int *host_ncfg);
+
+/* Autotuner: times the whole batch on the device.  First the grain (ranks
+ * per item: 1, 2, 4, ... up to 64 and 2R) with every class at its default
+ * shape; then, class by class from the largest FFT, every thread_mult and
+ * items_per_cta with the other classes at their best so far.  The winner is
+ * kept for this batch shape (sorted (FFT length, N, D, R, max I_n) of every
+ * problem) and used by later plans of the same shape created with grain 0;
+ * the grain goes to *host_best_grain; when the environment variable
+ * FCS_AUTOTUNE_CACHE names a file, the table is persisted there. */
 int fcs_batch_autotune(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
                        int *host_best_grain);
 

@@ -113,6 +113,13 @@ def lib() -> C.CDLL:
                                                   C.c_int]),
                 "fcs_batch_autotune": (C.c_int, [vp, C.c_int, C.POINTER(CpProblem),
                                                  C.POINTER(C.c_int)]),
+                "fcs_batch_plan_create_cfg": (C.c_int, [vp, C.c_int, C.POINTER(CpProblem),
+                                                        C.c_int, C.c_int,
+                                                        C.POINTER(BatchClassCfg),
+                                                        C.POINTER(C.c_void_p)]),
+                "fcs_batch_plan_config": (C.c_int, [vp, C.POINTER(C.c_int), C.c_int,
+                                                    C.POINTER(BatchClassCfg),
+                                                    C.POINTER(C.c_int)]),
                 "fcs_server_create": (C.c_int, [C.POINTER(ServerConfig),
                                                 C.POINTER(C.c_void_p)]),
                 "fcs_server_destroy": (C.c_int, [vp]),
@@ -142,6 +149,12 @@ class CpProblem(C.Structure):
                 ("U", C.c_void_p * 8), ("ldU", C.c_int64 * 8),
                 ("lam", C.c_void_p), ("h", C.c_void_p), ("s", C.c_void_p),
                 ("ldh", C.c_int64), ("out", C.c_void_p)]
+
+
+class BatchClassCfg(C.Structure):
+    """Mirror of `fcs_batch_class_cfg`."""
+    _fields_ = [("fft_len", C.c_int), ("thread_mult", C.c_int),
+                ("items_per_cta", C.c_int), ("threads", C.c_int)]
 
 
 FCS_REQ_CP = 0
@@ -193,6 +206,7 @@ def exported_symbols():
             "fcs_recover", "fcs_sketch_outer", "fcs_sketch_outer_sum",
             "fcs_batch_plan_create", "fcs_batch_plan_launch",
             "fcs_batch_plan_destroy", "fcs_batch_sketch_cp", "fcs_batch_autotune",
+            "fcs_batch_plan_create_cfg", "fcs_batch_plan_config",
             "fcs_server_create", "fcs_server_destroy", "fcs_server_submit",
             "fcs_server_poll", "fcs_server_wait", "fcs_server_cancel",
             "fcs_server_release", "fcs_server_stats", "fcs_server_reset_stats"]
@@ -716,15 +730,34 @@ class BatchPlan:
     `launch()` issues only device work on torch's current stream and may be
     captured into a CUDA graph."""
 
-    def __init__(self, ctx: Context, problems, grain: int = 0):
+    def __init__(self, ctx: Context, problems, grain: int = 0, classes=None):
+        """classes: None (autotuned or default shapes) or a list of
+        (fft_len, thread_mult, items_per_cta) per FFT-length class."""
         self.ctx = ctx
         self._arr = _problem_array(problems)
         h = C.c_void_p()
         ctx._sync_stream()
-        ctx.check(lib().fcs_batch_plan_create(ctx.handle, len(problems), self._arr,
-                                              grain, C.byref(h)))
+        if classes is None:
+            ctx.check(lib().fcs_batch_plan_create(ctx.handle, len(problems), self._arr,
+                                                  grain, C.byref(h)))
+        else:
+            cfg = (BatchClassCfg * max(1, len(classes)))(
+                *[BatchClassCfg(int(p), int(t), int(i), 0) for p, t, i in classes])
+            ctx.check(lib().fcs_batch_plan_create_cfg(ctx.handle, len(problems), self._arr,
+                                                      grain, len(classes), cfg, C.byref(h)))
         self._h = h
         ctx._plans.add(self)
+
+    def config(self):
+        """(grain, [(fft_len, thread_mult, items_per_cta, threads), ...]) the
+        plan was built with, largest FFT first."""
+        g, n = C.c_int(0), C.c_int(0)
+        buf = (BatchClassCfg * 16)()
+        ctx_check = lib().fcs_batch_plan_config(self._h, C.byref(g), 16, buf, C.byref(n))
+        if ctx_check != FCS_OK:
+            raise FcsError(ctx_check, "fcs_batch_plan_config failed")
+        return g.value, [(c.fft_len, c.thread_mult, c.items_per_cta, c.threads)
+                         for c in buf[:min(16, n.value)]]
 
     def launch(self):
         self.ctx._sync_stream()
@@ -762,6 +795,16 @@ def fcs_batch_autotune(ctx: Context, problems) -> int:
 def fcs_batch_plan_create(ctx: Context, problems, grain: int = 0) -> BatchPlan:
     """C-ABI-named alias of BatchPlan(ctx, problems, grain)."""
     return BatchPlan(ctx, problems, grain)
+
+
+def fcs_batch_plan_create_cfg(ctx: Context, problems, grain: int, classes) -> BatchPlan:
+    """C-ABI-named alias of BatchPlan(ctx, problems, grain, classes)."""
+    return BatchPlan(ctx, problems, grain, classes)
+
+
+def fcs_batch_plan_config(plan: BatchPlan):
+    """C-ABI-named alias of plan.config()."""
+    return plan.config()
 
 
 def fcs_batch_plan_launch(ctx: Context, plan: BatchPlan):

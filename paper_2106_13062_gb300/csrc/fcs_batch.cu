@@ -33,11 +33,11 @@
 #include <set>
 #include <vector>
 
-#include "fcs_batch_internal.cuh"
-#include "fcs_cp_run.cuh"
+#include "fcs_batch_kernels.cuh"
 
 struct fcs_batch_state {
-  std::map<uint64_t, int> tuned;   // batch signature -> grain
+  // batch signature -> autotuned grain and class shapes
+  std::map<uint64_t, std::pair<int, std::vector<fcs::ClassCfg>>> tuned;
   bool cache_loaded = false;
   std::set<fcs_batch_plan *> plans;   // live plans; detached when the context goes
 };
@@ -52,25 +52,11 @@ struct fcs_batch_plan {
   std::vector<fcs_cp_problem> longp;   // problems with P > 16384: their own launches
   void *long_ws = nullptr;             // their scratch, owned by the plan (graph-safe)
   size_t long_bytes = 0;
+  int grain = 0;                       // ranks per item it was built with
 };
 
 namespace fcs {
 namespace {
-
-struct BatchProb {
-  int N, D, L, sb;
-  int64_t R, rpi;
-  int64_t I[kMaxN], off[kMaxN], ut_off[kMaxN];
-  int64_t ldh, Jt;
-  const float *UT;
-  const int32_t *h;
-  const int8_t *s;
-  float2 *G;
-  unsigned *tickets;
-  float *out;
-  int groups;
-  int pad_;
-};
 
 struct TransposeTask {
   const float *U;
@@ -107,124 +93,13 @@ __global__ void batch_transpose_kernel(const TransposeTask *__restrict__ tasks, 
   }
 }
 
-// cp_run / cp13_run's accessors over a problem descriptor (fcs_cp_run.cuh).
-struct BatchView {
-  const BatchProb &P;
-  int sb;
-  __device__ __forceinline__ int modes() const { return P.N; }
-  __device__ __forceinline__ int64_t dim(int n) const { return P.I[n]; }
-  __device__ __forceinline__ const float *column(int n, int64_t r) const {
-    return P.UT + P.ut_off[n] + r * P.I[n];
-  }
-  __device__ __forceinline__ const int32_t *hashes(int d, int n) const {
-    return P.h + d * P.ldh + P.off[n];
-  }
-  __device__ __forceinline__ const int8_t *signs(int d, int n) const {
-    return P.s + d * P.ldh + P.off[n];
-  }
-  __device__ __forceinline__ int64_t length() const { return P.Jt; }
-  __device__ __forceinline__ float *sketch(int d) const { return P.out + d * P.Jt; }
-  __device__ __forceinline__ float2 *spectrum() const { return P.G; }
-  __device__ __forceinline__ unsigned *ticket(int d) const { return P.tickets + d; }
-};
-
-// Programmatic dependent launch.  launch_dependents lets the next launch of
-// the chain start once every CTA of this grid has issued it (so every CTA of
-// this grid is already resident: the next grid can never hold the SMs this
-// one still needs).  wait_previous returns once the previous grid of the
-// chain has completed and its writes are visible; called at a CTA's end, it
-// makes each grid complete after its predecessor, so work queued after the
-// chain waits for all of it.  Both are no-ops in a launch made without the
-// programmatic-serialisation attribute.
-__device__ __forceinline__ void pdl_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait_previous() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-// One CTA per item (problem, sketch d, rank group) of one FFT-size class,
-// P = 2^(LOG2M+1) <= 8192, NT = 2^(LOG2M-4) threads.
-template <int LOG2M, int NT, int CPT>
-__global__ void __launch_bounds__(NT) batch_class_kernel(const BatchProb *__restrict__ probs,
-                                                         const int4 *__restrict__ items,
-                                                         const float2 *__restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int is_last;
-  pdl_launch_dependents();
-  const int4 w = items[blockIdx.x];
-  const BatchProb &P = probs[w.x];
-  const int64_t r0 = int64_t(w.z) * P.rpi;
-  const int64_t r1 = min(P.R, r0 + P.rpi);
-  const BatchView view{P, P.sb};
-  cp_run<LOG2M, NT, CPT>(view, w.y, r0, r1, unsigned(P.groups), smem_raw, tw, &is_last);
-  pdl_wait_previous();
-}
-
-// The same for P = 16384 on the warp-DIT engine (ra <= 32 RMAX).
-template <int CPT, int RMAX>
-__global__ void __launch_bounds__(wdit::kNT) batch_class13_kernel(
-    const BatchProb *__restrict__ probs, const int4 *__restrict__ items,
-    const float2 *__restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int is_last;
-  pdl_launch_dependents();
-  const int4 w = items[blockIdx.x];
-  const BatchProb &P = probs[w.x];
-  const int64_t r0 = int64_t(w.z) * P.rpi;
-  const int64_t r1 = min(P.R, r0 + P.rpi);
-  const BatchView view{P, P.sb};
-  cp13_run<CPT, RMAX>(view, w.y, r0, r1, unsigned(P.groups), smem_raw, tw, &is_last);
-  pdl_wait_previous();
-}
-
-// Kernel, block size and shared memory of a class: FFT size L, prefetch
-// depth from the longest mode (entries per thread), scatter buffer sb.
-struct ClassKernel {
-  const void *fn;
-  int nt;
-  size_t smem;
-};
-
-template <int L>
-ClassKernel class_kernel_l(int cpt, int sb) {
-  constexpr int NT = fft_threads(L);
-  ClassKernel k{nullptr, NT, CpSmem<L, NT>::bytes(sb)};
-  if (cpt <= 1)
-    k.fn = reinterpret_cast<const void *>(batch_class_kernel<L, NT, 1>);
-  else if (cpt <= 2)
-    k.fn = reinterpret_cast<const void *>(batch_class_kernel<L, NT, 2>);
-  else
-    k.fn = reinterpret_cast<const void *>(batch_class_kernel<L, NT, 4>);
-  return k;
-}
-
-template <int CPT>
-const void *class13_fn(int ra) {
-  if (ra <= 128) return reinterpret_cast<const void *>(batch_class13_kernel<CPT, 4>);
-  if (ra <= 256) return reinterpret_cast<const void *>(batch_class13_kernel<CPT, 8>);
-  return reinterpret_cast<const void *>(batch_class13_kernel<CPT, 16>);
-}
-
-ClassKernel class_kernel(int L, int64_t Imax, int sb) {
-  if (L == wdit::kL) {
-    const int ra = (sb + 31) >> 5;
-    const int cpt = int((Imax + wdit::kNT - 1) / wdit::kNT);
-    const void *fn = cpt <= 1 ? class13_fn<1>(ra) : cpt <= 2 ? class13_fn<2>(ra) : class13_fn<4>(ra);
-    return ClassKernel{fn, wdit::kNT, Cp13Smem::bytes(ra)};
-  }
-  const int nt = fft_threads(L);
-  const int cpt = int((Imax + nt - 1) / nt);
-  switch (L) {
-#define FCS_CLASS_CASE(K) \
-  case K: return class_kernel_l<K>(cpt, sb);
-    FCS_CLASS_CASE(3) FCS_CLASS_CASE(4) FCS_CLASS_CASE(5) FCS_CLASS_CASE(6)
-    FCS_CLASS_CASE(7) FCS_CLASS_CASE(8) FCS_CLASS_CASE(9) FCS_CLASS_CASE(10)
-    FCS_CLASS_CASE(11) FCS_CLASS_CASE(12)
-#undef FCS_CLASS_CASE
-    default:
-      return ClassKernel{nullptr, 0, 0};
-  }
+// Class kernel for log2 M = L at thread multiplier ntm (slot FFT only; the
+// P = 16384 engine has one thread count) running ipc items per CTA.
+ClassKernel class_kernel(int L, int ntm, int ipc, int64_t Imax, int sb) {
+  if (L == wdit::kL) return class_kernel_13(ipc, Imax, sb);
+  if (L == 12) return class_kernel_12(ntm, ipc, Imax, sb);
+  if (L >= 10) return class_kernel_mid(L, ntm, ipc, Imax, sb);
+  return class_kernel_small(L, ntm, ipc, Imax, sb);
 }
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -284,6 +159,7 @@ uint64_t batch_signature(int nprob, const std::vector<HostProb> &hp,
   return x;
 }
 
+// Cache file: one line per batch signature, "sig grain L:ntm:ipc ...".
 void load_cache(fcs_batch_state &st) {
   if (st.cache_loaded) return;
   st.cache_loaded = true;
@@ -291,9 +167,21 @@ void load_cache(fcs_batch_state &st) {
   if (!path) return;
   FILE *f = fopen(path, "r");
   if (!f) return;
-  unsigned long long sig;
-  int g;
-  while (fscanf(f, "%llx %d", &sig, &g) == 2) st.tuned[sig] = g;
+  char line[4096];
+  while (fgets(line, sizeof(line), f)) {
+    unsigned long long sig;
+    int g, used = 0;
+    if (sscanf(line, "%llx %d%n", &sig, &g, &used) != 2) continue;
+    std::vector<ClassCfg> cfg;
+    const char *p = line + used;
+    ClassCfg c;
+    int n = 0;
+    while (sscanf(p, " %d:%d:%d%n", &c.L, &c.ntm, &c.ipc, &n) == 3) {
+      cfg.push_back(c);
+      p += n;
+    }
+    st.tuned[sig] = {g, cfg};
+  }
   fclose(f);
 }
 
@@ -302,7 +190,11 @@ void save_cache(const fcs_batch_state &st) {
   if (!path) return;
   FILE *f = fopen(path, "w");
   if (!f) return;
-  for (auto &kv : st.tuned) fprintf(f, "%016llx %d\n", (unsigned long long)kv.first, kv.second);
+  for (auto &kv : st.tuned) {
+    fprintf(f, "%016llx %d", (unsigned long long)kv.first, kv.second.first);
+    for (const ClassCfg &c : kv.second.second) fprintf(f, " %d:%d:%d", c.L, c.ntm, c.ipc);
+    fprintf(f, "\n");
+  }
   fclose(f);
 }
 
@@ -329,7 +221,8 @@ int default_grain(const fcs_ctx *ctx, int nprob, const fcs_cp_problem *q) {
 // grouped into FFT-size classes, largest first, each class's longest items
 // (ranks x modes) first.
 int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, char *base,
-                std::vector<char> *host_desc, BatchBuild *out) {
+                std::vector<char> *host_desc, BatchBuild *out,
+                const std::vector<ClassCfg> *cfg) {
   std::vector<HostProb> hp(nprob);
   for (int k = 0; k < nprob; ++k) {
     int rc = check_problem(ctx, k, q[k], &hp[k]);
@@ -436,14 +329,21 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
       Imax = std::max(Imax, hp[items[j].x].Imax);
       sb = std::max(sb, hp[items[j].x].sb);
     }
-    const ClassKernel ck = class_kernel(L, Imax, sb);
+    ClassCfg c{L, 1, 1};
+    if (cfg)
+      for (const ClassCfg &x : *cfg)
+        if (x.L == L) c = x;
+    if (L == wdit::kL || (c.ntm != 1 && c.ntm != 2)) c.ntm = 1;
+    if (c.ipc != 1 && c.ipc != 2 && c.ipc != 4) c.ipc = 1;
+    const ClassKernel ck = class_kernel(L, c.ntm, c.ipc, Imax, sb);
     if (!ck.fn) return set_error(ctx, FCS_EUNSUPPORTED, "no batch kernel for log2 M = %d", L);
     if (ck.smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(ck.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            int(ck.smem));
       if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(batch class)");
     }
-    bb.classes.push_back(BatchClass{ck.fn, ck.nt, ck.smem, int(i), int(j - i)});
+    bb.classes.push_back(
+        BatchClass{ck.fn, ck.nt, ck.smem, int(i), int(j - i), L, c.ntm, c.ipc});
     i = j;
   }
   if (tiles > 0x7fffffffLL) return set_error(ctx, FCS_EUNSUPPORTED, "batch too large");
@@ -474,8 +374,9 @@ int batch_issue(fcs_ctx *ctx, char *base, const BatchBuild &b) {
   for (size_t c = 0; c < b.classes.size(); ++c) {
     const BatchClass &k = b.classes[c];
     const int4 *items = reinterpret_cast<const int4 *>(base + b.items_off) + k.first;
+    int count = k.count, ipc = k.ipc;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(k.count));
+    cfg.gridDim = dim3(unsigned((k.count + k.ipc - 1) / k.ipc));
     cfg.blockDim = dim3(unsigned(k.nt));
     cfg.dynamicSmemBytes = k.smem;
     cfg.stream = ctx->stream;
@@ -484,7 +385,7 @@ int batch_issue(fcs_ctx *ctx, char *base, const BatchBuild &b) {
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = c > 0 ? 1 : 0;
-    void *args[] = {&probs, &items, &tw};
+    void *args[] = {&probs, &items, &tw, &count, &ipc};
     rc = check_cuda(ctx, cudaLaunchKernelExC(&cfg, k.fn, args), "batch_class_kernel");
     if (rc) return rc;
   }
@@ -500,7 +401,7 @@ namespace {
 // Build a plan: lay the batch out in plan-owned device memory and upload the
 // descriptors.
 int plan_create(fcs_ctx *ctx, int nprob_all, const fcs_cp_problem *q_all, int grain,
-                fcs_batch_plan **out) {
+                fcs_batch_plan **out, const std::vector<ClassCfg> *cfg = nullptr) {
   *out = nullptr;
   // problems with P > 16384 run after the batch kernels, each with the
   // multi-kernel long-FFT route
@@ -515,7 +416,7 @@ int plan_create(fcs_ctx *ctx, int nprob_all, const fcs_cp_problem *q_all, int gr
   const fcs_cp_problem *q = shortp.data();
   BatchBuild bb{};
   std::vector<char> desc;
-  int rc = nprob ? batch_build(ctx, nprob, q, grain, nullptr, &desc, &bb) : FCS_OK;
+  int rc = nprob ? batch_build(ctx, nprob, q, grain, nullptr, &desc, &bb, cfg) : FCS_OK;
   if (rc) return rc;
   if (ctx->ws_bytes + ctx->plan_bytes + bb.total > ctx->budget)
     return set_error(ctx, FCS_ENOMEM_BUDGET,
@@ -530,7 +431,7 @@ int plan_create(fcs_ctx *ctx, int nprob_all, const fcs_cp_problem *q_all, int gr
       delete plan;
       return check_cuda(ctx, e, "cudaMalloc(batch plan)");
     }
-    rc = batch_build(ctx, nprob, q, grain, static_cast<char *>(plan->dev), &desc, &bb);
+    rc = batch_build(ctx, nprob, q, grain, static_cast<char *>(plan->dev), &desc, &bb, cfg);
     if (rc == FCS_OK)
       rc = check_cuda(ctx,
                       cudaMemcpy(plan->dev, desc.data(), desc.size(), cudaMemcpyHostToDevice),
@@ -575,6 +476,7 @@ int plan_create(fcs_ctx *ctx, int nprob_all, const fcs_cp_problem *q_all, int gr
     plan->outs.emplace_back(q_all[k].out, sizeof(float) * size_t(q_all[k].D) * size_t(jt));
   }
   plan->build = bb;
+  plan->grain = grain;
   ctx->plan_bytes += bb.total + plan->long_bytes;
   ctx->batch->plans.insert(plan);
   *out = plan;
@@ -611,13 +513,33 @@ void plan_free(fcs_batch_plan *plan) {
   delete plan;
 }
 
-int resolve_grain(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain) {
-  if (grain > 0) return grain;
+// The autotuned entry of this batch shape, or null.
+const std::pair<int, std::vector<ClassCfg>> *tuned_entry(fcs_ctx *ctx, int nprob,
+                                                         const fcs_cp_problem *q) {
   std::vector<HostProb> hp(nprob);
   for (int k = 0; k < nprob; ++k)
-    if (check_problem(ctx, k, q[k], &hp[k]) != FCS_OK) return -1;
+    if (check_problem(ctx, k, q[k], &hp[k]) != FCS_OK) return nullptr;
   auto it = ctx->batch->tuned.find(batch_signature(nprob, hp, q));
-  return it != ctx->batch->tuned.end() ? it->second : default_grain(ctx, nprob, q);
+  return it != ctx->batch->tuned.end() ? &it->second : nullptr;
+}
+
+// Device time of `reps` launches of a plan after one warm-up (ms, summed).
+int time_plan(fcs_ctx *ctx, fcs_batch_plan *plan, cudaEvent_t e0, cudaEvent_t e1, int reps,
+              float *ms_out) {
+  int rc = plan_launch(ctx, plan);
+  float total = 0.f;
+  for (int rep = 0; rep < reps && rc == FCS_OK; ++rep) {
+    cudaEventRecord(e0, ctx->stream);
+    rc = plan_launch(ctx, plan);
+    cudaEventRecord(e1, ctx->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    total += ms;
+  }
+  cudaStreamSynchronize(ctx->stream);
+  *ms_out = total;
+  return rc;
 }
 
 }  // namespace
@@ -655,9 +577,52 @@ extern "C" int fcs_batch_plan_create(fcs_ctx *ctx, int nprob, const fcs_cp_probl
   int rc = ensure_batch_state(ctx);
   if (rc) return rc;
   DeviceGuard g(ctx->device);
-  grain = resolve_grain(ctx, nprob, host_probs, grain);
-  if (grain < 1) return ctx->err.empty() ? set_error(ctx, FCS_EINVAL, "invalid batch") : FCS_EINVAL;
-  return plan_create(ctx, nprob, host_probs, grain, plan);
+  // the autotuned shape of this batch (grain and class shapes), if any
+  const auto *t = tuned_entry(ctx, nprob, host_probs);
+  if (grain < 1) grain = t ? t->first : default_grain(ctx, nprob, host_probs);
+  return plan_create(ctx, nprob, host_probs, grain, plan, t ? &t->second : nullptr);
+}
+
+extern "C" int fcs_batch_plan_create_cfg(fcs_ctx *ctx, int nprob,
+                                         const fcs_cp_problem *host_probs, int grain, int ncfg,
+                                         const fcs_batch_class_cfg *host_cfg,
+                                         fcs_batch_plan **plan) {
+  if (!ctx || !plan) return FCS_EINVAL;
+  *plan = nullptr;
+  ctx->err.clear();
+  if (nprob < 1 || !host_probs) return set_error(ctx, FCS_EINVAL, "empty batch");
+  if (ncfg < 0 || (ncfg > 0 && !host_cfg)) return set_error(ctx, FCS_EINVAL, "bad class list");
+  std::vector<ClassCfg> cfg;
+  for (int c = 0; c < ncfg; ++c) {
+    const fcs_batch_class_cfg &x = host_cfg[c];
+    const int L = ilog2_ceil(x.fft_len) - 1;
+    if (x.fft_len < 16 || x.fft_len > (1 << kMaxLog2P) || (x.fft_len & (x.fft_len - 1)))
+      return set_error(ctx, FCS_EINVAL, "class %d: fft_len %d is not a power of two in [16, %d]",
+                       c, x.fft_len, 1 << kMaxLog2P);
+    if (x.thread_mult != 1 && !(x.thread_mult == 2 && L < wdit::kL))
+      return set_error(ctx, FCS_EINVAL, "class %d: thread_mult %d not available", c,
+                       x.thread_mult);
+    if (x.items_per_cta != 1 && x.items_per_cta != 2 && x.items_per_cta != 4)
+      return set_error(ctx, FCS_EINVAL, "class %d: items_per_cta %d not in {1,2,4}", c,
+                       x.items_per_cta);
+    cfg.push_back(ClassCfg{L, x.thread_mult, x.items_per_cta});
+  }
+  int rc = ensure_batch_state(ctx);
+  if (rc) return rc;
+  DeviceGuard g(ctx->device);
+  if (grain < 1) grain = default_grain(ctx, nprob, host_probs);
+  return plan_create(ctx, nprob, host_probs, grain, plan, &cfg);
+}
+
+extern "C" int fcs_batch_plan_config(const fcs_batch_plan *plan, int *host_grain, int max_cfg,
+                                     fcs_batch_class_cfg *host_cfg, int *host_ncfg) {
+  if (!plan || !host_ncfg || (max_cfg > 0 && !host_cfg)) return FCS_EINVAL;
+  const auto &cls = plan->build.classes;
+  *host_ncfg = int(cls.size());
+  if (host_grain) *host_grain = plan->grain;
+  for (int c = 0; c < int(cls.size()) && c < max_cfg; ++c)
+    host_cfg[c] = fcs_batch_class_cfg{2 << cls[c].L, cls[c].ntm, cls[c].ipc, cls[c].nt};
+  return FCS_OK;
 }
 
 extern "C" int fcs_batch_plan_launch(fcs_ctx *ctx, const fcs_batch_plan *plan) {
@@ -701,43 +666,66 @@ extern "C" int fcs_batch_autotune(fcs_ctx *ctx, int nprob, const fcs_cp_problem 
   DeviceGuard g(ctx->device);
   std::vector<HostProb> hp(nprob);
   int64_t rmax = 1;
+  std::set<int> sizes;                       // FFT-size classes of the batch kernels
   for (int k = 0; k < nprob; ++k) {
     rc = check_problem(ctx, k, host_probs[k], &hp[k]);
     if (rc) return rc;
     rmax = std::max<int64_t>(rmax, hp[k].R);
+    if (!hp[k].longp) sizes.insert(hp[k].L);
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return set_error(ctx, FCS_ECUDA, "cudaEventCreate");
+  // the whole batch timed on the device for each candidate
+  auto timed = [&](int grain, const std::vector<ClassCfg> &cfg, float *ms) -> int {
+    fcs_batch_plan *plan = nullptr;
+    int r = plan_create(ctx, nprob, host_probs, grain, &plan, &cfg);
+    if (r) return r;
+    r = time_plan(ctx, plan, e0, e1, 3, ms);
+    plan_free(plan);
+    return r;
+  };
+  // 1. ranks per item, every class at its default shape
+  std::vector<ClassCfg> cfg;
+  for (int L : sizes) cfg.push_back(ClassCfg{L, 1, 1});
   int best = 1;
   float best_ms = 1e30f;
-  for (int grain = 1; grain <= 64 && grain < 2 * rmax; grain *= 2) {
-    fcs_batch_plan *plan = nullptr;
-    rc = plan_create(ctx, nprob, host_probs, grain, &plan);
-    if (rc) break;
-    rc = plan_launch(ctx, plan);                        // warm-up
-    float total = 0.f;
-    for (int rep = 0; rep < 3 && rc == FCS_OK; ++rep) {
-      cudaEventRecord(e0, ctx->stream);
-      rc = plan_launch(ctx, plan);
-      cudaEventRecord(e1, ctx->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      total += ms;
-    }
-    cudaStreamSynchronize(ctx->stream);
-    plan_free(plan);
-    if (rc) break;
-    if (total < best_ms) {
-      best_ms = total;
+  for (int grain = 1; grain <= 64 && grain < 2 * rmax && rc == FCS_OK; grain *= 2) {
+    float ms = 0.f;
+    rc = timed(grain, cfg, &ms);
+    if (rc == FCS_OK && ms < best_ms) {
+      best_ms = ms;
       best = grain;
     }
+  }
+  // 2. per class, threads per transform and items per CTA, the other
+  //    classes held at their best so far (one sweep, largest FFT first); a
+  //    shape replaces the current one only if it is at least 3 % faster
+  for (auto c = cfg.rbegin(); c != cfg.rend() && rc == FCS_OK; ++c) {
+    const ClassCfg keep = *c;
+    ClassCfg bestc = keep;
+    for (int ntm : {1, 2}) {
+      if (ntm == 2 && c->L == wdit::kL) continue;
+      for (int ipc : {1, 2, 4}) {
+        if (ntm == keep.ntm && ipc == keep.ipc) continue;
+        c->ntm = ntm;
+        c->ipc = ipc;
+        float ms = 0.f;
+        rc = timed(best, cfg, &ms);
+        if (rc) break;
+        if (ms < 0.97f * best_ms) {              // a clear gain, not timing noise
+          best_ms = ms;
+          bestc = *c;
+        }
+      }
+      if (rc) break;
+    }
+    *c = bestc;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  ctx->batch->tuned[batch_signature(nprob, hp, host_probs)] = best;
+  ctx->batch->tuned[batch_signature(nprob, hp, host_probs)] = {best, cfg};
   save_cache(*ctx->batch);
   if (host_best_grain) *host_best_grain = best;
   return FCS_OK;

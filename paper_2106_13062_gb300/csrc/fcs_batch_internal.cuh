@@ -8,12 +8,21 @@
 
 namespace fcs {
 
+// Tunable shape of one FFT-size class (log2 M = L): thread multiplier ntm
+// (1 or 2; the slot FFT runs M/16 or M/8 threads, at least a warp; fixed at
+// 1 for the P = 16384 engine) and items run one after another per CTA (ipc:
+// 1, 2 or 4).
+struct ClassCfg {
+  int L, ntm, ipc;
+};
+
 // One launch of a batch: the items [first, first + count) of one FFT size.
 struct BatchClass {
   const void *fn;            // kernel
   int nt;                    // threads per CTA
   size_t smem;               // dynamic shared memory per CTA
   int first, count;
+  int L, ntm, ipc;           // the configuration it was built with
 };
 
 // Layout of one batch in device memory (see batch_build).
@@ -28,8 +37,11 @@ struct BatchBuild {
 };
 
 // Lay the batch out at device address `base` (NULL: sizes only, in *out).
+// cfg (may be NULL) gives the shape of each FFT-size class it names; other
+// classes take ntm = 1, ipc = 1.
 int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, char *base,
-                std::vector<char> *host_desc, BatchBuild *out);
+                std::vector<char> *host_desc, BatchBuild *out,
+                const std::vector<ClassCfg> *cfg = nullptr);
 // Clear accumulators, transpose factors, run the class kernels on
 // ctx->stream; the descriptor image must already be at `base`.
 int batch_issue(fcs_ctx *ctx, char *base, const BatchBuild &b);

@@ -191,6 +191,7 @@ extern "C" int fcs_destroy(fcs_ctx *ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->raw) cudaFree(ctx->raw);
   if (ctx->algo) cudaFree(ctx->algo);
+  if (ctx->switch_ev) cudaEventDestroy(ctx->switch_ev);
   if (ctx->twiddle) cudaFree(ctx->twiddle);
   delete ctx;
   return FCS_OK;
@@ -198,7 +199,28 @@ extern "C" int fcs_destroy(fcs_ctx *ctx) {
 
 extern "C" int fcs_set_stream(fcs_ctx *ctx, void *stream) {
   if (!ctx) return FCS_EINVAL;
-  ctx->stream = static_cast<cudaStream_t>(stream);
+  cudaStream_t next = static_cast<cudaStream_t>(stream);
+  if (next == ctx->stream) return FCS_OK;
+  // work queued so far may still use the context's buffers: the new stream
+  // waits for it (no host synchronisation).  Skipped while either stream is
+  // being captured into a CUDA graph, where the capture itself orders the work.
+  DeviceGuard g(ctx->device);
+  cudaStreamCaptureStatus c0 = cudaStreamCaptureStatusNone, c1 = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &c0) != cudaSuccess ||
+      cudaStreamIsCapturing(next, &c1) != cudaSuccess ||
+      c0 != cudaStreamCaptureStatusNone || c1 != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    ctx->stream = next;
+    return FCS_OK;
+  }
+  if (!ctx->switch_ev) {
+    cudaError_t e = cudaEventCreateWithFlags(&ctx->switch_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaEventCreate");
+  }
+  cudaError_t e = cudaEventRecord(ctx->switch_ev, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(next, ctx->switch_ev, 0);
+  if (e != cudaSuccess) return check_cuda(ctx, e, "fcs_set_stream");
+  ctx->stream = next;
   return FCS_OK;
 }
 

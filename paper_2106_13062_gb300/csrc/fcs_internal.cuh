@@ -38,6 +38,7 @@ struct fcs_ctx {
   size_t raw_bytes = 0;
   void *algo = nullptr;          // scratch of fcs_rtpm / fcs_als
   size_t algo_bytes = 0;
+  cudaEvent_t switch_ev = nullptr;   // orders a new stream after the old one
   std::string err;
 };
 
@@ -62,6 +63,7 @@ int check_cuda(fcs_ctx *ctx, cudaError_t e, const char *what);
 int ensure_workspace(fcs_ctx *ctx, size_t bytes, void **out);
 // Grow ctx->raw to at least `bytes` (counted against the budget with the workspace).
 int ensure_raw(fcs_ctx *ctx, size_t bytes);
+
 
 // RAII guard that makes ctx->device current for the duration of a call.
 struct DeviceGuard {

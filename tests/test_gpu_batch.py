@@ -162,3 +162,83 @@ def test_plan_outliving_its_context(fcs):
     plan = fcs.BatchPlan(c2, probs2)
     c2.close()
     assert not plan._h.value
+
+
+CLASS_SHAPES = [(1, 1), (2, 1), (1, 2), (2, 2), (1, 4), (2, 4)]
+
+
+@pytest.mark.parametrize("ntm,ipc", CLASS_SHAPES)
+def test_every_class_shape_matches_single_calls(fcs, ctx, ntm, ipc):
+    """Each thread multiplier and items-per-CTA count the autotuner may pick,
+    applied to every FFT-length class of the batch (P = 16 ... 16384; the
+    P = 16384 engine takes thread multiplier 1 only), gives each problem's
+    fcs_sketch_cp result."""
+    probs, refs, keep = _make(fcs, ctx, seed=21)
+    lens = sorted({1 << max(4, (sum(J) - len(J)).bit_length()) for _, _, _, _, _, _, _, _, J
+                   in keep}, reverse=True)
+    classes = [(P, ntm if P < 16384 else 1, ipc) for P in lens]
+    plan = fcs.BatchPlan(ctx, probs, grain=2, classes=classes)
+    grain, got = plan.config()
+    assert grain == 2
+    assert [(p, t, i) for p, t, i, _ in got] == classes
+    plan.launch()
+    torch.cuda.synchronize()
+    for k, ref in enumerate(refs):
+        assert_sketch_close(host(keep[k][6]), host(ref), what=f"shape {ntm}x{ipc} problem {k}")
+    plan.close()
+
+
+def _uniform_batch(fcs, ctx, n, I, J, R, D, seed):
+    probs, refs, keep = [], [], []
+    for k in range(n):
+        U, lam = synth.cp_factors(seed + k, I, R)
+        Ug, lamg = [cuda(u) for u in U], cuda(lam)
+        h, s = fcs.fcs_make_hashes(ctx, seed + 500 + k, I, J, D)
+        pr, out = fcs.cp_problem(Ug, lamg, J, h, s)
+        probs.append(pr)
+        refs.append(fcs.fcs_sketch_cp(ctx, Ug, lamg, J, h, s))
+        keep.append((Ug, lamg, h, s, out))
+    return probs, refs, keep
+
+
+def test_autotuner_picks_class_shapes(fcs, tmp_path):
+    """Two batch shapes are autotuned: 400 tiny problems (P = 32, rank 1, one
+    sketch: many light items, all resident at once) and two problems whose
+    few items carry long columns (P = 2048, I_n = 2000, rank 2, two
+    sketches: the Count Sketch of 2000 entries per column dominates, so twice
+    the threads per transform should pay).  The plans created afterwards
+    with grain 0 carry exactly the grain and class shapes the tuner stored
+    (read back from the cache file), the two batch shapes get different
+    class shapes, and every result equals fcs_sketch_cp's."""
+    path = str(tmp_path / "fcs_tune_classes.txt")
+    os.environ["FCS_AUTOTUNE_CACHE"] = path
+    try:
+        c = fcs.Context()
+        chosen = []
+        for n, I, J, R, D, seed in [(400, [6, 5, 7], [10, 11, 9], 1, 1, 1000),
+                                    (2, [2000, 2000, 2000], [300, 400, 350], 2, 2, 2000)]:
+            probs, refs, keep = _uniform_batch(fcs, c, n, I, J, R, D, seed)
+            g = fcs.fcs_batch_autotune(c, probs)
+            plan = fcs.BatchPlan(c, probs)               # grain 0: the tuned entry
+            grain, cls = plan.config()
+            assert grain == g and len(cls) == 1
+            P, ntm, ipc, nt = cls[0]
+            assert ntm in (1, 2) and ipc in (1, 2, 4) and nt >= 32
+            # the cache file holds the same choice
+            stored = {}
+            for line in open(path):
+                tok = line.split()
+                stored[int(tok[1])] = stored.get(int(tok[1]), []) + [tuple(
+                    int(x) for x in t.split(":")) for t in tok[2:]]
+            assert any((P.bit_length() - 2, ntm, ipc) in v for v in stored.values())
+            plan.launch()
+            torch.cuda.synchronize()
+            for k, ref in enumerate(refs):
+                assert_sketch_close(host(keep[k][4]), host(ref), what=f"tuned P={P} {k}")
+            plan.close()
+            chosen.append((P, ntm, ipc, grain))
+        print(f"\nautotuned (P, threads x, items per CTA, grain): {chosen}")
+        assert chosen[0][1:3] != chosen[1][1:3], chosen
+        c.close()
+    finally:
+        del os.environ["FCS_AUTOTUNE_CACHE"]

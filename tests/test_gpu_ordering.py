@@ -191,3 +191,20 @@ def test_graph_reads_batch_outputs_after_the_chain(fcs, ctx, orc):
         for k, (snap, ref) in enumerate(zip(snaps, refs)):
             assert_sketch_close(host(snap), ref, what=f"graph snapshot {k}")
     plan.close()
+
+
+def test_persistent_accumulator_across_sketch_counts(fcs, orc):
+    """Calls at P = 16384 with D = 16, 1 and 7 (and ranks fewer than the
+    groups of a sketch) in a row on a fresh context reuse one workspace for
+    the spectrum accumulator and tickets: each must start from zero."""
+    c = fcs.Context()
+    Is, Js = [60, 50, 40], [4000, 4000, 4000]            # Jt = 11998, P = 16384
+    outs, refs = [], []
+    for k, (R, D) in enumerate([(3, 16), (9, 1), (2, 7), (5, 16)]):
+        U, lam = synth.cp_factors(600 + k, Is, R)
+        h, s = fcs.fcs_make_hashes(c, 700 + k, Is, Js, D)
+        outs.append(fcs.fcs_sketch_cp(c, [cuda(u) for u in U], cuda(lam), Js, h, s))
+        refs.append(_ref(orc, U, lam, Js, 700 + k, D))
+    for k in range(len(outs)):
+        assert_sketch_close(host(outs[k]), refs[k], what=f"call {k}")
+    c.close()
