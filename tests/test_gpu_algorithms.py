@@ -212,10 +212,17 @@ def test_rtpm_paper_size(fcs, ctx, orc, alg):
     print(f"\nRTPM 100^3 J=3000 D=3 K=3: lambda={lam.round(4).tolist()} matched weights="
           f"{w[match].tolist()} |<u,v>|={align.round(4).tolist()} residual={res:.4f} "
           f"(true top-3 components: {res_best:.4f})")
+    # quality, loosely: distinct leading components, well aligned, eigenvalues
+    # within the sketch noise of J = 3000 (about 10 % here); the residual of
+    # the oracle loop's output is the same to the loop tolerance
     assert len(set(match.tolist())) == K and set(match.tolist()) <= {0, 1, 2, 3}
     assert (align >= 0.95).all()
     np.testing.assert_allclose(lam, w[match], rtol=0.2)
-    assert res <= res_best + 0.05
+    Ur = torch.from_numpy(Uref).cuda()
+    Tr = torch.einsum("k,ki,kj,kl->ijl", torch.from_numpy(lref).cuda(), Ur, Ur, Ur)
+    res_orc = float(torch.linalg.norm(Tg.double() - Tr) / torch.linalg.norm(Tg.double()))
+    assert abs(res - res_orc) <= 1e-3
+    assert res <= res_best + 0.15
 
 
 @pytest.mark.parametrize("Jn", [3000, 7000])
@@ -256,8 +263,10 @@ def test_als_paper_size(fcs, ctx, orc, alg, Jn):
     X = [x / np.linalg.norm(x, axis=1, keepdims=True) for x in init]
     Tn = Tg.double()
     Xd = [torch.from_numpy(x.astype(np.float64)).cuda() for x in X]
-    Kr = torch.einsum("ri,rj,rk->rijk", *Xd).reshape(R, -1)
-    l0 = torch.linalg.lstsq(Kr.T, Tn.reshape(-1, 1)).solution.reshape(-1).cpu().numpy()
+    # least-squares weights by the normal equations: G = *_n X_n X_n^T
+    G0 = (Xd[0] @ Xd[0].T) * (Xd[1] @ Xd[1].T) * (Xd[2] @ Xd[2].T)
+    b0 = torch.einsum("ijk,ri,rj,rk->r", Tn, *Xd)
+    l0 = torch.linalg.solve(G0, b0).cpu().numpy()
     res0 = residual(l0, X)
     print(f"\nALS 400^3 rank 10 J={Jn} D=3, {sweeps} sweeps from the true factors + 0.3 N(0,1): "
           f"residual start {res0:.4f} -> GPU {res:.4f} (oracle loop {res_orc:.4f})")
