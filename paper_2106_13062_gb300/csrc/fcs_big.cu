@@ -457,6 +457,207 @@ __global__ void __launch_bounds__(kNT1) cp15_kernel(Cp15Args a, const float2 *__
   }
 }
 
+// The same items on the warp-DIT engine for M = 2^14 (wdit::w15, 512
+// threads): per transform, the Count Sketch goes into a 32-row scatter
+// buffer, each warp runs the 512-point FFTs of two rows, one block barrier,
+// then thread t takes column q2(t), twiddles it, runs a 32-point DFT and the
+// real-FFT unpack (lane shuffles), leaving TWICE the 32 half-spectrum values
+// X[(j < 16 ? q2 : q2_partner(q2)) + 512 j] in registers.  The running
+// product of the rank's modes is kept in the CTA's L2 slice (thread t's value
+// pair c at prod[c * 512 + t]), the last mode's product is added to G_d with
+// atomics, and the next column is scattered between the barriers, as in the
+// P = 16384 engine.  G_d therefore holds 2^N times the spectrum, and the
+// inverse scales by 2^-N.  The inverse runs on the same engine in place in
+// the FFT buffer.  Hash ranges up to 32 * 2 * kRaMax15 real bins fit the
+// scatter buffer (ra = ceil(max J_n / 64) <= kRaMax15).
+struct Cp15wSmem {
+  static constexpr size_t kB = 0;                                   // 32 x kRS float2
+  static constexpr size_t kTw = kB + sizeof(float2) * 32 * wdit::kRS;
+  static constexpr size_t kStash = kTw + sizeof(float2) * wdit::w15::kTwLen;
+  static constexpr size_t kA = kStash + sizeof(float2) * 32;
+  static size_t bytes(int ra) { return kA + sizeof(float2) * 32 * size_t(ra); }
+};
+constexpr int kRaMax15 = int((232448 - 1024 - Cp15wSmem::kA) / (sizeof(float2) * 32));   // 1 KiB for static shared memory
+
+template <int CPT, int RMAX>
+__global__ void __launch_bounds__(wdit::kNT) cp15w_kernel(Cp15Args a, const float2 *__restrict__ tw,
+                                                          int ra) {
+  namespace W = wdit::w15;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int is_last;
+  constexpr int NT = wdit::kNT, M = W::kM, HALF = M / 2;
+  float2 *B = reinterpret_cast<float2 *>(smem + Cp15wSmem::kB);
+  float2 *tws = reinterpret_cast<float2 *>(smem + Cp15wSmem::kTw);
+  float2 *stash = reinterpret_cast<float2 *>(smem + Cp15wSmem::kStash);
+  float2 *A2 = reinterpret_cast<float2 *>(smem + Cp15wSmem::kA);
+  float *A = reinterpret_cast<float *>(A2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int N = a.m.N;
+  const int q2 = wdit::q2_of(tid), q2p = wdit::q2_partner(q2);
+  float4 *prod = a.prod + int64_t(blockIdx.x) * HALF;
+  W::fill_twiddles(tws, tw);
+  for (int e = tid; e < 32 * ra; e += NT) A2[e] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const int items = a.D * a.groups;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int d = item / a.groups, g = item - d * a.groups;
+    const int64_t r0 = a.R * g / a.groups, r1 = a.R * (g + 1) / a.groups;
+    float2 *Gd = a.G + int64_t(d) * (M + 1);
+    // column (r, n): signed factor values (lambda on mode 0) and hash bins
+    float pv[CPT];
+    int ph[CPT];
+    auto fetch = [&](int64_t r, int n) {
+      const int64_t In = a.m.I[n], ld = a.ldU[n];
+      const float *col = a.U[n] + r;
+      const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
+      const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
+      const float w = (n == 0 && a.lambda) ? __ldg(a.lambda + r) : 1.f;
+      const int Jn = a.m.J[n];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const int64_t i = tid + int64_t(c) * NT;
+        ph[c] = -1;
+        pv[c] = 0.f;
+        if (i < In) {
+          const float v = __ldg(col + i * ld) * w;
+          pv[c] = __ldg(sn + i) < 0 ? -v : v;
+          const int hb = __ldg(hn + i);
+          ph[c] = unsigned(hb) < unsigned(Jn) ? hb : -1;
+        }
+      }
+    };
+    auto scatter = [&](int64_t r, int n) {
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+        if (ph[c] >= 0) atomicAdd(A + W::a_index(ph[c], ra), pv[c]);
+      const int64_t In = a.m.I[n];
+      if (In > int64_t(CPT) * NT) {
+        const int64_t ld = a.ldU[n];
+        const float *col = a.U[n] + r;
+        const int32_t *hn = a.h + d * a.m.ldh + a.m.off[n];
+        const int8_t *sn = a.s + d * a.m.ldh + a.m.off[n];
+        const float w = (n == 0 && a.lambda) ? __ldg(a.lambda + r) : 1.f;
+        const int Jn = a.m.J[n];
+        for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
+          const int hb = __ldg(hn + i);
+          const float v = __ldg(col + i * ld) * w;
+          if (unsigned(hb) < unsigned(Jn))
+            atomicAdd(A + W::a_index(hb, ra), __ldg(sn + i) < 0 ? -v : v);
+        }
+      }
+    };
+    fetch(r0, 0);
+    scatter(r0, 0);
+    __syncthreads();
+    for (int64_t r = r0; r < r1; ++r) {
+      for (int n = 0; n < N; ++n) {
+        int64_t rn = r;
+        int nn = n + 1;
+        if (nn == N) {
+          nn = 0;
+          ++rn;
+        }
+        const bool more = rn < r1;
+        if (more) fetch(rn, nn);
+        W::step1_row<RMAX, false, false>(A2 + warp * ra, ra, B + warp * wdit::kRS, tws, warp);
+        W::step1_row<RMAX, false, false>(A2 + (warp + 16) * ra, ra, B + (warp + 16) * wdit::kRS,
+                                         tws, warp + 16);
+        __syncthreads();
+        // half the warps scatter the next column before step 2, half after
+        const bool early = tid < NT / 2;
+        if (more && early) scatter(rn, nn);
+        float2 v[32];
+        W::step2(B, tws, stash, v);
+        const bool first = n == 0, last = n == N - 1;
+#pragma unroll
+        for (int c0 = 0; c0 < 16; c0 += 4) {
+          float4 pp[4];
+          if (!first) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) pp[c] = __ldcg(prod + (c0 + c) * NT + tid);
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int j = 2 * (c0 + c);
+            if (!first) {
+              v[j] = slot_mul(make_float2(pp[c].x, pp[c].y), v[j], tid == 0 && j == 0);
+              v[j + 1] = cmul(make_float2(pp[c].z, pp[c].w), v[j + 1]);
+            }
+            if (!last) {
+              __stcg(prod + (c0 + c) * NT + tid, make_float4(v[j].x, v[j].y, v[j + 1].x, v[j + 1].y));
+            } else {
+#pragma unroll
+              for (int k = 0; k < 2; ++k) {
+                const int jj = j + k;
+                const int bin = (jj < 16 ? q2 : q2p) + 512 * jj;
+                if (tid == 0 && jj == 0) {
+                  atomicAdd(&Gd[0].x, v[0].x);      // bins 0 and M, both real
+                  atomicAdd(&Gd[M].x, v[0].y);
+                } else {
+                  atomicAdd(&Gd[bin], v[jj]);
+                }
+              }
+            }
+          }
+        }
+        if (more && !early) scatter(rn, nn);
+        __syncthreads();
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(a.ticket + d, 1u) == unsigned(a.groups - 1);
+    __syncthreads();
+    if (is_last) {
+      __threadfence();
+      // conj-packed sequence of the summed spectrum, row-swizzled into B
+      for (int k0 = 0; k0 < HALF / NT; k0 += 8) {
+        float2 Av[8], Bv[8], Wv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int q = (k0 + k) * NT + tid;
+          if (q == 0) {
+            Av[k] = make_float2(__ldcg(&Gd[0].x), __ldcg(&Gd[M].x));
+            Bv[k] = __ldcg(&Gd[HALF]);
+            Wv[k] = make_float2(1.f, 0.f);
+          } else {
+            Av[k] = __ldcg(&Gd[q]);
+            Bv[k] = __ldcg(&Gd[M - q]);
+            Wv[k] = __ldg(&tw[q]);                   // W_P^q, P = 2^15
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int q = (k0 + k) * NT + tid;
+          float2 cq, cm;
+          pack_pair_conj_values_w(q, Av[k], Bv[k], Wv[k], cq, cm);
+          B[W::row_pos_swz(q)] = cq;
+          B[W::row_pos_swz(q ? M - q : HALF)] = cm;
+        }
+      }
+      __syncthreads();
+      W::step1_row<16, true, true>(B + warp * wdit::kRS, 512, B + warp * wdit::kRS, tws, warp);
+      W::step1_row<16, true, true>(B + (warp + 16) * wdit::kRS, 512,
+                                   B + (warp + 16) * wdit::kRS, tws, warp + 16);
+      __syncthreads();
+      float2 v[32];
+      W::step2_complex(B, tws, v);                  // v[q1] = Z[q2 + 512 q1]
+      // 1/M of the inverse and 2^-N for the doubled unpack of every mode
+      const float sc = 1.0f / (float(M) * float(1 << N));
+      float *od = a.out + int64_t(d) * a.m.Jt;
+      const int64_t Jt = a.m.Jt;
+#pragma unroll
+      for (int q1 = 0; q1 < 32; ++q1) {
+        const int64_t m = q2 + 512 * q1;
+        if (2 * m < Jt) od[2 * m] = v[q1].x * sc;
+        if (2 * m + 1 < Jt) od[2 * m + 1] = -v[q1].y * sc;
+      }
+      if (tid == 0) a.ticket[d] = 0u;
+    }
+    __syncthreads();                                  // B is reused by the next item
+  }
+}
+
 // ---------------------------------------------------------------- contractions
 // Half spectra of T transforms Z [T][M] into S [T][M+1] (bin 0 and M real).
 __global__ void half_spectrum_kernel(const float2 *__restrict__ Z, int64_t M,
@@ -697,6 +898,35 @@ int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *c
       a.out = out;
       int rc = check_cuda(ctx, cudaMemsetAsync(ws, 0, f.gbytes, ctx->stream), "cudaMemsetAsync(G)");
       if (rc) return rc;
+      int64_t jmax = 1, imax = 1;
+      for (int n = 0; n < N; ++n) {
+        jmax = std::max<int64_t>(jmax, m.J[n]);
+        imax = std::max<int64_t>(imax, m.I[n]);
+      }
+      const int ra = int((jmax + 63) >> 6);
+      if (ra <= kRaMax15) {
+        // the warp-DIT engine: scatter buffer of 32 rows of ra float2
+        const int cpt = int((imax + wdit::kNT - 1) / wdit::kNT);
+        const void *kern;
+        if (ra <= 128)
+          kern = cpt <= 1   ? reinterpret_cast<const void *>(cp15w_kernel<1, 4>)
+                 : cpt <= 2 ? reinterpret_cast<const void *>(cp15w_kernel<2, 4>)
+                            : reinterpret_cast<const void *>(cp15w_kernel<4, 4>);
+        else
+          kern = cpt <= 1   ? reinterpret_cast<const void *>(cp15w_kernel<1, 8>)
+                 : cpt <= 2 ? reinterpret_cast<const void *>(cp15w_kernel<2, 8>)
+                            : reinterpret_cast<const void *>(cp15w_kernel<4, 8>);
+        const size_t smem = Cp15wSmem::bytes(ra);
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp15w)");
+        const float2 *twp = ctx->twiddle;
+        int rap = ra;
+        void *args[] = {&a, &twp, &rap};
+        e = cudaLaunchKernel(kern, dim3(unsigned(f.ctas)), dim3(wdit::kNT), args, smem,
+                             ctx->stream);
+        return check_cuda(ctx, e, "cp15w_kernel");
+      }
       const size_t smem = sizeof(float2) * padded_len(kM2);
       cudaError_t e = cudaFuncSetAttribute(cp15_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            int(smem));

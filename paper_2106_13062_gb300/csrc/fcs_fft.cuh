@@ -668,6 +668,167 @@ __device__ __forceinline__ void step2(const float2 *B, const float2 *tws, float2
   }
 }
 
+// ---------------------------------------------------------------- M = 2^14
+// The same decomposition for M = 16384 (P = 32768): z[32 m2 + w] for 32
+// sub-sequences w of 512 points.  Step 1 runs the 512-point FFT of row w
+// exactly as above (each of the 16 warps takes rows w and w + 16); step 2
+// gives thread t column q2 = q2_of(t) of the 32 x 512 result, twiddles it by
+// W_M^(w q2) and takes a 32-point DFT over w, so that v[q1] = Z[q2 + 512 q1];
+// the real-FFT unpack pairs (q, M - q) again span lanes l and l ^ 16.
+namespace w15 {
+
+constexpr int kRows = 32;
+constexpr int kM = 1 << 14;
+constexpr int kTw2 = 16 * 32;               // after the step-1 table W512^(l ka)
+constexpr int kTwLen = kTw2 + 6 * kNT;      // W_M^(q2 2^b), b < 5; W_P^q2
+
+// Float index of real sample h in the 32-row scatter buffer (row m mod 32,
+// column m / 32 for m = h / 2; rows of ra float2).
+__device__ __forceinline__ int a_index(int h, int ra) {
+  const int m = h >> 1;
+  return 2 * ((m & 31) * ra + (m >> 5)) + (h & 1);
+}
+
+// Position of z[m] in a 32-row buffer of row stride kRS whose rows are
+// XOR-swizzled (row w holds z[32 m2 + w] at column m2 ^ w); read back by
+// step1_row<16, true, true>.
+__device__ __forceinline__ int row_pos_swz(int m) {
+  const int w = m & 31;
+  return w * kRS + ((m >> 5) ^ w);
+}
+
+// Per-CTA twiddle table: the step-1 part as in wdit::fill_twiddles, then for
+// thread t W_M^(q2(t) 2^b) at kTw2 + b*512 + t (b < 5) and W_P^q2(t) at
+// kTw2 + 5*512 + t, from tw[k] = exp(-2 pi i k / 2^15).  Called by all kNT
+// threads; every load is issued before the first store.
+__device__ __forceinline__ void fill_twiddles(float2 *tws, const float2 *__restrict__ tw) {
+  constexpr int PER = kTwLen / kNT;
+  static_assert(kTwLen % kNT == 0, "twiddle table fill");
+  float2 v[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int e = threadIdx.x + k * kNT;
+    if (e < kTw2) {
+      const int ka = e >> 5, l = e & 31;
+      v[k] = __ldg(&tw[(l * ka) << (kLogTwN - 9)]);
+    } else {
+      const int b = (e - kTw2) >> 9, q2 = q2_of((e - kTw2) & (kNT - 1));
+      v[k] = b < 5 ? __ldg(&tw[(q2 << b) << (kLogTwN - 14)]) : __ldg(&tw[q2]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) tws[threadIdx.x + k * kNT] = v[k];
+}
+
+// Step 1 for row w: the 512-point FFT of in_row (ra float2 entries; with SWZ
+// column c of row w sits at c ^ w) into out_row (kRS float2, also the
+// transpose scratch).  INPLACE: in_row == out_row, so the warp synchronises
+// after reading its input and nothing is cleared; otherwise the entries read
+// are cleared.  No block barrier inside.
+template <int RMAX, bool SWZ, bool INPLACE>
+__device__ __forceinline__ void step1_row(float2 *in_row, int ra, float2 *out_row,
+                                          const float2 *tws, int w) {
+  const int l = threadIdx.x & 31;
+  const int lc = SWZ ? (l ^ w) : l;
+  float2 v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int m2 = l + 32 * r;
+    v[r] = (r < RMAX && m2 < ra) ? in_row[lc + 32 * r] : make_float2(0.f, 0.f);
+  }
+  if (INPLACE) {
+    __syncwarp();
+  } else {
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const int m2 = l + 32 * r;
+      if (m2 < ra) in_row[lc + 32 * r] = make_float2(0.f, 0.f);
+    }
+  }
+  DftNZ<16, RMAX>::run(v);
+#pragma unroll
+  for (int ka = 1; ka < 16; ++ka) v[ka] = cmul(v[ka], tws[ka * 32 + l]);   // W512^(l ka)
+  float2 *T = out_row;
+#pragma unroll
+  for (int ka = 0; ka < 16; ka += 2)
+    *reinterpret_cast<float4 *>(T + l * kTR + ka) =
+        make_float4(v[ka].x, v[ka].y, v[ka + 1].x, v[ka + 1].y);
+  __syncwarp();
+  const int j = l & 15;
+  const bool odd = l >= 16;
+  const float sg = odd ? -1.f : 1.f;
+#pragma unroll
+  for (int lp = 0; lp < 16; ++lp) {
+    const float2 a = T[lp * kTR + j], b = T[(lp + 16) * kTR + j];
+    float2 g = make_float2(fmaf(sg, b.x, a.x), fmaf(sg, b.y, a.y));
+    if (lp > 0) {
+      const float2 wv = unit64(2 * lp);
+      g = cmul(g, make_float2(odd ? wv.x : 1.f, odd ? wv.y : 0.f));
+    }
+    v[lp] = g;
+  }
+  Dft<16>::run(v);
+  __syncwarp();
+  const int k0 = j + (odd ? 16 : 0);
+#pragma unroll
+  for (int kk = 0; kk < 16; ++kk) T[k0 + 32 * kk] = v[kk];
+}
+
+// Step 2 up to the complex spectrum: v[q1] = Z[q2 + 512 q1], q2 = q2_of(t).
+__device__ __forceinline__ void step2_complex(const float2 *B, const float2 *tws,
+                                              float2 (&v)[32]) {
+  const int t = threadIdx.x;
+  const int q2 = q2_of(t);
+#pragma unroll
+  for (int w = 0; w < 32; ++w) v[w] = B[w * kRS + q2];
+  {
+    float2 wp[5];                                   // W_M^(q2 2^b)
+#pragma unroll
+    for (int b = 0; b < 5; ++b) wp[b] = tws[kTw2 + b * kNT + t];
+    twiddle_powers<5>(v, wp);
+  }
+  Dft<32>::run(v);
+}
+
+// Step 2 with the real-FFT unpack: v[j] = TWICE the half-spectrum value
+// X[(j < 16 ? q2 : q2_partner(q2)) + 512 j]; thread 0 holds X[512 j], with
+// v[0] packing the two real bins (2 X[0], 2 X[M]).  `stash` is 32 float2 of
+// shared scratch for thread 0.  Every lane of every warp must call it.
+__device__ __forceinline__ void step2(const float2 *B, const float2 *tws, float2 *stash,
+                                      float2 (&v)[32]) {
+  const int t = threadIdx.x;
+  step2_complex(B, tws, v);
+  if (t == 0) {
+#pragma unroll
+    for (int q1 = 0; q1 < 32; ++q1) stash[q1] = v[q1];
+  }
+  const int lane = t & 31;
+  const bool self = t < 32 && (lane & 15) == 0;     // q2 = 0 or 256
+  const int src = self ? lane : (lane ^ 16);
+  const float2 wP = tws[kTw2 + 5 * kNT + t];        // W_P^q2, P = 32768
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    // Z[M - (q2 + 512 i)] = Z[q2p + 512 (31 - i)] is the partner's v[31 - i]
+    float2 zm;
+    zm.x = __shfl_sync(0xffffffffu, v[31 - i].x, src);
+    zm.y = __shfl_sync(0xffffffffu, v[31 - i].y, src);
+    // W_P^(q2 + 512 i) = W_P^q2 exp(-2 pi i i / 64)
+    const float2 wq = i == 0 ? wP : cmul(wP, unit64(i));
+    unpack2_twice(v[i], zm, wq, v[i], v[31 - i]);
+  }
+  if (t == 0) {
+    // q2 = 0: Z[512 q1] pairs with Z[512 (32 - q1)]; q1 = 0 and 16 pair with themselves
+    const float2 z0 = stash[0], z16 = stash[16];
+    v[0] = make_float2(2.f * (z0.x + z0.y), 2.f * (z0.x - z0.y));
+    v[16] = make_float2(2.f * z16.x, -2.f * z16.y);
+#pragma unroll
+    for (int q1 = 1; q1 < 16; ++q1)
+      unpack2_twice(stash[q1], stash[32 - q1], unit64(q1), v[q1], v[32 - q1]);
+  }
+}
+
+}  // namespace w15
+
 }  // namespace wdit
 
 }  // namespace fcs

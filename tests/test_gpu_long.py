@@ -44,6 +44,10 @@ def _cp(fcs, ctx, orc, I, J, R, D, seed, budget_ctx=None):
     ([200, 300, 250], [8192, 8192, 8192], 5, 3),      # Jt = 24574, P = 2^15 (fused kernel)
     ([20000], [20000], 3, 2),                         # one mode: its transform is also the last
     ([400, 300, 500, 200], [9000, 7000, 5000, 6000], 40, 10),   # 150 items of 2-3 ranks
+    ([300, 400], [9000, 9000], 3, 2),                 # P = 2^15, two modes
+    ([1500, 300, 200], [13700, 2000, 1500], 6, 3),    # P = 2^15 at the widest scatter buffer
+    ([2500, 100, 100], [9000, 5000, 4000], 3, 2),     # P = 2^15, a mode longer than 4 x 512
+    ([300, 200, 100], [14000, 2000, 1000], 4, 2),     # P = 2^15 past it: the block-FFT kernel
     ([300, 400], [20000, 15000], 3, 2),               # Jt = 34999, P = 2^16
     ([3000], [300000], 2, 2),                         # P = 2^19
     ([5000], [1 << 20], 2, 1),                        # Jt = 2^20 = P, the largest
