@@ -216,32 +216,22 @@ class CpWorkload:
 
     def e2e_prepare(self):
         """Inputs staged as one pinned host buffer [U_1 | ... | U_N | lambda]
-        and copied to one device buffer per step (one transfer, not N + 1);
-        the library gets views of it."""
+        whose views go to fcs_sketch_cp_host (the library merges the adjacent
+        ranges into one copy), output into a pinned host buffer."""
         import torch
         parts = [u.reshape(-1) for u in self.host["U"]] + [self.host["lam"]]
         self.inh = torch.from_numpy(np.concatenate(parts)).pin_memory()
-        self.ind = torch.empty(self.inh.shape, dtype=torch.float32, device=self.dev)
         offs = np.cumsum([0] + [p.size for p in parts])
-        self.Ud = [self.ind[offs[n]:offs[n + 1]].view(self.I, self.R) for n in range(self.N)]
-        self.lamd = self.ind[offs[self.N]:offs[self.N + 1]]
+        self.Uh = [self.inh[offs[n]:offs[n + 1]].view(self.I, self.R) for n in range(self.N)]
+        self.lamh = self.inh[offs[self.N]:offs[self.N + 1]]
         self.outh = torch.empty((self.D, self.Jt), dtype=torch.float32).pin_memory()
-        self.copy_stream = torch.cuda.Stream(device=self.dev)
         return self.inh.numel() * 4, self.outh.numel() * 4
 
     def e2e_step(self, k):
-        """The input copy runs on a side stream (after everything queued so
-        far) while the hash tables are generated; the sketch waits for both."""
-        import torch
-        fcs = self.fcs
-        main = torch.cuda.current_stream(self.dev)
-        self.copy_stream.wait_stream(main)
-        with torch.cuda.stream(self.copy_stream):
-            self.ind.copy_(self.inh, non_blocking=True)
-        h, s = fcs.fcs_make_hashes(self.ctx, self.seed + k, self.Is, self.Js, self.D)
-        main.wait_stream(self.copy_stream)
-        fcs.fcs_sketch_cp(self.ctx, self.Ud, self.lamd, self.Js, h, s, out=self.out)
-        self.outh.copy_(self.out, non_blocking=True)
+        """One library call with host buffers: copies in, hash tables from
+        the seed, the sketch, and the copy out, all on the current stream."""
+        self.fcs.fcs_sketch_cp_host(self.ctx, self.Uh, self.lamh, self.Js, self.D,
+                                    self.seed + k, out=self.outh)
 
     def check(self):
         import torch

@@ -43,7 +43,8 @@
  *    launch chain and longer problems with the launches above.
  *  - The library allocates only its own context workspace (device memory
  *    reused across calls, bounded by the context's budget), a 256 KiB
- *    twiddle table and, when enabled, the spectrum cache of fcs_contract.
+ *    twiddle table, the staging buffer of fcs_sketch_cp_host when that is
+ *    used and, when enabled, the spectrum cache of fcs_contract.
  *    A context must be used from one host thread at a time.
  *  - Floating point is FP32 throughout; sums use atomics, so the last bits
  *    of a result may differ from run to run.  Hashes and bins are exact.
@@ -157,6 +158,25 @@ int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
                   const float *const *host_U, const int64_t *host_ldU,
                   const float *lambda, const int32_t *h, const int8_t *s,
                   int64_t ldh, float *out);
+
+/*
+ * fcs_sketch_cp_host -- fcs_sketch_cp from and to HOST memory, with the hash
+ * tables generated from `seed` (as fcs_make_hashes would, bit for bit).
+ *   host_U[N]: HOST pointers, U_n is I_n x R FP32 row-major with leading
+ *   dimension host_ldU[n] >= R; host_lambda: HOST [R] or NULL (all ones);
+ *   host_out: HOST [D][Jt] FP32.
+ * The call queues on the context's stream: the host-to-device copies of the
+ * factors and lambda (ranges that follow each other in host memory move in
+ * one copy; pinned memory makes them asynchronous), the hash generation, the
+ * sketch, and the device-to-host copy of the result, which is complete once
+ * the stream has been synchronised.  The inputs must stay unchanged until
+ * then.  Device staging of 4*(sum_n I_n*R + R) + 5*D*sum_n I_n + 4*D*Jt bytes
+ * (each part rounded up to 256) is held by the context (within its budget,
+ * beside the workspace fcs_sketch_cp uses).
+ */
+int fcs_sketch_cp_host(fcs_ctx *ctx, int N, const int64_t *host_I, const int32_t *host_J,
+                       int64_t R, int D, const float *const *host_U, const int64_t *host_ldU,
+                       const float *host_lambda, uint64_t seed, float *host_out);
 
 /*
  * fcs_sketch_cp_noalloc -- fcs_sketch_cp for callers that cannot allocate

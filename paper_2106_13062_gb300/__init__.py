@@ -73,6 +73,9 @@ def lib() -> C.CDLL:
                 "fcs_sketch_cp": (C.c_int, [vp, C.c_int, i64p, i32p, C.c_int64,
                                             C.c_int, C.POINTER(C.c_void_p), i64p,
                                             vp, vp, vp, C.c_int64, vp]),
+                "fcs_sketch_cp_host": (C.c_int, [vp, C.c_int, i64p, i32p, C.c_int64,
+                                                 C.c_int, C.POINTER(C.c_void_p), i64p,
+                                                 vp, C.c_uint64, vp]),
                 "fcs_sketch_cp_noalloc": (C.c_int, [vp, C.c_int, i64p, i32p,
                                                     C.c_int64, C.c_int,
                                                     C.POINTER(C.c_void_p), i64p,
@@ -200,7 +203,7 @@ def exported_symbols():
     """Names of the C entry points this binding expects libfcs.so to export."""
     return ["fcs_version", "fcs_create", "fcs_destroy", "fcs_set_stream",
             "fcs_last_error", "fcs_workspace_bytes", "fcs_make_hashes",
-            "fcs_sketch_dense", "fcs_sketch_cp", "fcs_sketch_cp_noalloc",
+            "fcs_sketch_dense", "fcs_sketch_cp", "fcs_sketch_cp_noalloc", "fcs_sketch_cp_host",
             "fcs_contract", "fcs_contract_both", "fcs_cache_spectra", "fcs_forget",
             "fcs_fold", "fcs_sketch_inner", "fcs_rtpm", "fcs_als",
             "fcs_recover", "fcs_sketch_outer", "fcs_sketch_outer_sum",
@@ -428,6 +431,41 @@ def fcs_sketch_cp(ctx: Context, U, lam, J, h, s, ldh: int = 0,
         ctx.handle, N, _arr(C.c_int64, [u.shape[0] for u in U]),
         _arr(C.c_int32, J), R, D, ptrs, _arr(C.c_int64, [u.stride(0) for u in U]),
         _ptr(lam), _ptr(h), _ptr(s), ldh, _ptr(out)))
+    return out
+
+
+def fcs_sketch_cp_host(ctx: Context, U, lam, J, D: int, seed: int,
+                       out: torch.Tensor | None = None):
+    """CP-route FCS from host factors to a host sketch (fcs_sketch_cp_host):
+    U_n are CPU float32 tensors I_n x R with unit column stride (pinned ones
+    make the copies asynchronous), lam a CPU [R] tensor or None; hash tables
+    from `seed` as fcs_make_hashes.  Returns the CPU [D, Jt] output (given or
+    allocated pinned); it is complete once torch's current stream of the
+    context's device has been synchronised."""
+    ctx._sync_stream()
+    N = len(U)
+    if N < 1 or len(J) != N:
+        raise ValueError("need one hash length J_n per factor matrix")
+    R = U[0].shape[1]
+    for k, u in enumerate(U):
+        if not isinstance(u, torch.Tensor) or u.is_cuda or u.dtype != torch.float32:
+            raise TypeError(f"U[{k}] must be a CPU float32 tensor")
+        if u.dim() != 2 or u.shape[1] != R or u.stride(1) != 1:
+            raise ValueError("each U_n must be I_n x R with unit column stride")
+    if lam is not None:
+        if lam.is_cuda or lam.dtype != torch.float32 or lam.numel() < R or not lam.is_contiguous():
+            raise ValueError("lambda must be a contiguous CPU float32 tensor of at least R entries")
+    Jt = jtilde(J)
+    if out is None:
+        out = torch.empty((D, Jt), dtype=torch.float32).pin_memory()
+    if out.is_cuda or out.dtype != torch.float32 or not out.is_contiguous() or out.numel() < D * Jt:
+        raise ValueError("out must be a contiguous CPU float32 tensor of D x Jt entries")
+    ptrs = (C.c_void_p * N)(*[u.data_ptr() for u in U])
+    ctx.check(lib().fcs_sketch_cp_host(
+        ctx.handle, N, _arr(C.c_int64, [u.shape[0] for u in U]), _arr(C.c_int32, J), R, int(D),
+        ptrs, _arr(C.c_int64, [u.stride(0) for u in U]),
+        None if lam is None else C.c_void_p(lam.data_ptr()), C.c_uint64(int(seed)),
+        C.c_void_p(out.data_ptr())))
     return out
 
 

@@ -192,6 +192,7 @@ extern "C" int fcs_destroy(fcs_ctx *ctx) {
   if (ctx->raw) cudaFree(ctx->raw);
   if (ctx->algo) cudaFree(ctx->algo);
   if (ctx->switch_ev) cudaEventDestroy(ctx->switch_ev);
+  if (ctx->stage) cudaFree(ctx->stage);
   if (ctx->twiddle) cudaFree(ctx->twiddle);
   delete ctx;
   return FCS_OK;

@@ -39,6 +39,8 @@ struct fcs_ctx {
   void *algo = nullptr;          // scratch of fcs_rtpm / fcs_als
   size_t algo_bytes = 0;
   cudaEvent_t switch_ev = nullptr;   // orders a new stream after the old one
+  void *stage = nullptr;             // device staging of fcs_sketch_cp_host
+  size_t stage_bytes = 0;
   std::string err;
 };
 
