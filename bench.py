@@ -615,8 +615,16 @@ class BatchWorkload:
             pr, out = fcs.cp_problem(Ug, lamg, J, h, s, out=out)
             probs.append(pr)
             self.items.append((Ug, lamg, h, s, out, J))
-        self.grain = fcs.fcs_batch_autotune(ctx, probs)
-        self.plan = fcs.BatchPlan(ctx, probs, grain=self.grain)
+        # the tuning table of an earlier run is reused when FCS_AUTOTUNE_CACHE
+        # names an existing file (the plan then takes the stored grain and
+        # class shapes); otherwise the batch is autotuned here
+        cache = os.environ.get("FCS_AUTOTUNE_CACHE")
+        if cache and os.path.exists(cache):
+            self.plan = fcs.BatchPlan(ctx, probs)
+            self.grain = self.plan.config()[0]
+        else:
+            self.grain = fcs.fcs_batch_autotune(ctx, probs)
+            self.plan = fcs.BatchPlan(ctx, probs, grain=self.grain)
         self.plan.launch()
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
@@ -679,7 +687,10 @@ class BatchWorkload:
                 "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak,
                 "traffic": profiled_traffic("batch_class_kernels_mixed64.txt",
-                                            ["fcs_batch.cu", "fcs_cp_run.cuh", "fcs_fft.cuh",
+                                            ["fcs_batch.cu", "fcs_batch_kernels.cuh",
+                                             "fcs_batch_k0.cu", "fcs_batch_k1.cu",
+                                             "fcs_batch_k2.cu", "fcs_batch_k3.cu",
+                                             "fcs_batch_k4.cu", "fcs_cp_run.cuh", "fcs_fft.cuh",
                                              "fcs_internal.cuh"]),
                 "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes "
                                f"x 2 flop/FMA x {sm_mhz:.0f} MHz",
