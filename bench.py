@@ -695,8 +695,9 @@ class BatchWorkload:
                 "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes "
                                f"x 2 flop/FMA x {sm_mhz:.0f} MHz",
                 "avg_launch_ms": t, "grain": self.grain,
-                "classes": [{"fft_len": P, "thread_mult": m, "items_per_cta": i, "threads": n}
-                            for P, m, i, n in self.plan.config()[1]],
+                "classes": [{"fft_len": P, "engine": "warp-DIT" if e else "slot FFT",
+                             "thread_mult": m, "items_per_cta": i, "threads": n}
+                            for P, m, i, n, e in self.plan.config()[1]],
                 "plain_per_problem_ms": plain_ms,
                 "plain_sketches_per_s": self.sketches_per_step() / (plain_ms / 1e3),
                 "batched_over_plain": plain_ms / t}

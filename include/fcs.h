@@ -267,20 +267,25 @@ int fcs_batch_plan_destroy(fcs_batch_plan *plan);
 int fcs_batch_sketch_cp(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
                         int grain);
 
-/* Shape of one FFT-length class of a batch plan.  thread_mult: 1 = one
+/* Shape of one FFT-length class of a batch plan.  engine: 0 = the slot FFT
+ * (Stockham passes in shared memory, P <= 8192), 1 = the warp-DIT engine
+ * (512-point sub-FFTs per warp, then a column step per thread; P = 8192 and
+ * P = 16384, the only engine there).  thread_mult (slot FFT only): 1 = one
  * radix-16 butterfly per thread (P/32 threads, at least 32), 2 = twice as
- * many threads (P <= 8192 only).  items_per_cta: 1, 2 or 4 work items run one
- * after another by each CTA.  threads: the block size that results (output
- * of fcs_batch_plan_config, ignored on input). */
+ * many threads.  items_per_cta: 1, 2 or 4 work items run one after another by
+ * each CTA.  threads: the block size that results (output of
+ * fcs_batch_plan_config, ignored on input). */
 typedef struct fcs_batch_class_cfg {
   int fft_len;              /* P, a power of two in [16, 16384] */
+  int engine;
   int thread_mult;
   int items_per_cta;
   int threads;
 } fcs_batch_class_cfg;
 
 /* fcs_batch_plan_create with explicit class shapes (classes not listed take
- * thread_mult = 1, items_per_cta = 1) and grain (0 = the default grain). */
+ * the slot FFT -- warp-DIT for P = 16384 -- with thread_mult = 1 and
+ * items_per_cta = 1) and grain (0 = the default grain). */
 int fcs_batch_plan_create_cfg(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
                               int grain, int ncfg, const fcs_batch_class_cfg *host_cfg,
                               fcs_batch_plan **plan);
@@ -292,8 +297,10 @@ int fcs_batch_plan_config(const fcs_batch_plan *plan, int *host_grain, int max_c
 
 /* Autotuner: times the whole batch on the device.  First the grain (ranks
  * per item: 1, 2, 4, ... up to 64 and 2R) with every class at its default
- * shape; then, class by class from the largest FFT, every thread_mult and
- * items_per_cta with the other classes at their best so far.  The winner is
+ * shape; then, class by class from the largest FFT, every engine (for
+ * P = 8192), thread_mult and items_per_cta with the other classes at their
+ * best so far, a shape replacing the current one only when at least 3 %
+ * faster.  The winner is
  * kept for this batch shape (sorted (FFT length, N, D, R, max I_n) of every
  * problem) and used by later plans of the same shape created with grain 0;
  * the grain goes to *host_best_grain; when the environment variable

@@ -156,7 +156,7 @@ class CpProblem(C.Structure):
 
 class BatchClassCfg(C.Structure):
     """Mirror of `fcs_batch_class_cfg`."""
-    _fields_ = [("fft_len", C.c_int), ("thread_mult", C.c_int),
+    _fields_ = [("fft_len", C.c_int), ("engine", C.c_int), ("thread_mult", C.c_int),
                 ("items_per_cta", C.c_int), ("threads", C.c_int)]
 
 
@@ -770,7 +770,8 @@ class BatchPlan:
 
     def __init__(self, ctx: Context, problems, grain: int = 0, classes=None):
         """classes: None (autotuned or default shapes) or a list of
-        (fft_len, thread_mult, items_per_cta) per FFT-length class."""
+        (fft_len, thread_mult, items_per_cta[, engine]) per FFT-length class;
+        engine 0 = slot FFT, 1 = warp-DIT (default: 1 for P = 16384, else 0)."""
         self.ctx = ctx
         self._arr = _problem_array(problems)
         h = C.c_void_p()
@@ -779,22 +780,25 @@ class BatchPlan:
             ctx.check(lib().fcs_batch_plan_create(ctx.handle, len(problems), self._arr,
                                                   grain, C.byref(h)))
         else:
-            cfg = (BatchClassCfg * max(1, len(classes)))(
-                *[BatchClassCfg(int(p), int(t), int(i), 0) for p, t, i in classes])
+            def one(c):
+                p, t, i = (int(x) for x in c[:3])
+                e = int(c[3]) if len(c) > 3 else (1 if p == 16384 else 0)
+                return BatchClassCfg(p, e, t, i, 0)
+            cfg = (BatchClassCfg * max(1, len(classes)))(*[one(c) for c in classes])
             ctx.check(lib().fcs_batch_plan_create_cfg(ctx.handle, len(problems), self._arr,
                                                       grain, len(classes), cfg, C.byref(h)))
         self._h = h
         ctx._plans.add(self)
 
     def config(self):
-        """(grain, [(fft_len, thread_mult, items_per_cta, threads), ...]) the
-        plan was built with, largest FFT first."""
+        """(grain, [(fft_len, thread_mult, items_per_cta, threads, engine), ...])
+        the plan was built with, largest FFT first."""
         g, n = C.c_int(0), C.c_int(0)
         buf = (BatchClassCfg * 16)()
         ctx_check = lib().fcs_batch_plan_config(self._h, C.byref(g), 16, buf, C.byref(n))
         if ctx_check != FCS_OK:
             raise FcsError(ctx_check, "fcs_batch_plan_config failed")
-        return g.value, [(c.fft_len, c.thread_mult, c.items_per_cta, c.threads)
+        return g.value, [(c.fft_len, c.thread_mult, c.items_per_cta, c.threads, c.engine)
                          for c in buf[:min(16, n.value)]]
 
     def launch(self):

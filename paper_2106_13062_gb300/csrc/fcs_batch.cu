@@ -95,9 +95,9 @@ __global__ void batch_transpose_kernel(const TransposeTask *__restrict__ tasks, 
 
 // Class kernel for log2 M = L at thread multiplier ntm (slot FFT only; the
 // P = 16384 engine has one thread count) running ipc items per CTA.
-ClassKernel class_kernel(int L, int ntm, int ipc, int64_t Imax, int sb) {
+ClassKernel class_kernel(int L, int eng, int ntm, int ipc, int64_t Imax, int sb) {
   if (L == wdit::kL) return class_kernel_13(ipc, Imax, sb);
-  if (L == 12) return class_kernel_12(ntm, ipc, Imax, sb);
+  if (L == 12) return class_kernel_12(eng, ntm, ipc, Imax, sb);
   if (L >= 10) return class_kernel_mid(L, ntm, ipc, Imax, sb);
   return class_kernel_small(L, ntm, ipc, Imax, sb);
 }
@@ -159,7 +159,8 @@ uint64_t batch_signature(int nprob, const std::vector<HostProb> &hp,
   return x;
 }
 
-// Cache file: one line per batch signature, "sig grain L:ntm:ipc ...".
+// Cache file: one line per batch signature, "sig grain L:ntm:ipc:eng ..."
+// (a missing engine field reads as 0).
 void load_cache(fcs_batch_state &st) {
   if (st.cache_loaded) return;
   st.cache_loaded = true;
@@ -174,9 +175,11 @@ void load_cache(fcs_batch_state &st) {
     if (sscanf(line, "%llx %d%n", &sig, &g, &used) != 2) continue;
     std::vector<ClassCfg> cfg;
     const char *p = line + used;
-    ClassCfg c;
-    int n = 0;
-    while (sscanf(p, " %d:%d:%d%n", &c.L, &c.ntm, &c.ipc, &n) == 3) {
+    while (true) {
+      ClassCfg c;
+      int n = 0, n4 = 0;
+      if (sscanf(p, " %d:%d:%d%n", &c.L, &c.ntm, &c.ipc, &n) != 3) break;
+      if (sscanf(p + n, ":%d%n", &c.eng, &n4) == 1) n += n4;
       cfg.push_back(c);
       p += n;
     }
@@ -192,7 +195,8 @@ void save_cache(const fcs_batch_state &st) {
   if (!f) return;
   for (auto &kv : st.tuned) {
     fprintf(f, "%016llx %d", (unsigned long long)kv.first, kv.second.first);
-    for (const ClassCfg &c : kv.second.second) fprintf(f, " %d:%d:%d", c.L, c.ntm, c.ipc);
+    for (const ClassCfg &c : kv.second.second)
+      fprintf(f, " %d:%d:%d:%d", c.L, c.ntm, c.ipc, c.eng);
     fprintf(f, "\n");
   }
   fclose(f);
@@ -329,13 +333,14 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
       Imax = std::max(Imax, hp[items[j].x].Imax);
       sb = std::max(sb, hp[items[j].x].sb);
     }
-    ClassCfg c{L, 1, 1};
+    ClassCfg c{L, 1, 1, L == wdit::kL ? 1 : 0};
     if (cfg)
       for (const ClassCfg &x : *cfg)
         if (x.L == L) c = x;
-    if (L == wdit::kL || (c.ntm != 1 && c.ntm != 2)) c.ntm = 1;
+    c.eng = L == wdit::kL ? 1 : (L == 12 && c.eng == 1 ? 1 : 0);
+    if (c.eng == 1 || (c.ntm != 1 && c.ntm != 2)) c.ntm = 1;
     if (c.ipc != 1 && c.ipc != 2 && c.ipc != 4) c.ipc = 1;
-    const ClassKernel ck = class_kernel(L, c.ntm, c.ipc, Imax, sb);
+    const ClassKernel ck = class_kernel(L, c.eng, c.ntm, c.ipc, Imax, sb);
     if (!ck.fn) return set_error(ctx, FCS_EUNSUPPORTED, "no batch kernel for log2 M = %d", L);
     if (ck.smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(ck.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -343,7 +348,7 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
       if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(batch class)");
     }
     bb.classes.push_back(
-        BatchClass{ck.fn, ck.nt, ck.smem, int(i), int(j - i), L, c.ntm, c.ipc});
+        BatchClass{ck.fn, ck.nt, ck.smem, int(i), int(j - i), L, c.ntm, c.ipc, c.eng});
     i = j;
   }
   if (tiles > 0x7fffffffLL) return set_error(ctx, FCS_EUNSUPPORTED, "batch too large");
@@ -599,13 +604,18 @@ extern "C" int fcs_batch_plan_create_cfg(fcs_ctx *ctx, int nprob,
     if (x.fft_len < 16 || x.fft_len > (1 << kMaxLog2P) || (x.fft_len & (x.fft_len - 1)))
       return set_error(ctx, FCS_EINVAL, "class %d: fft_len %d is not a power of two in [16, %d]",
                        c, x.fft_len, 1 << kMaxLog2P);
-    if (x.thread_mult != 1 && !(x.thread_mult == 2 && L < wdit::kL))
+    const int eng_ok = L == wdit::kL ? x.engine == 1 : L == 12 ? (x.engine == 0 || x.engine == 1)
+                                                               : x.engine == 0;
+    if (!eng_ok)
+      return set_error(ctx, FCS_EINVAL, "class %d: engine %d not available for P = %d", c,
+                       x.engine, x.fft_len);
+    if (x.thread_mult != 1 && !(x.thread_mult == 2 && x.engine == 0))
       return set_error(ctx, FCS_EINVAL, "class %d: thread_mult %d not available", c,
                        x.thread_mult);
     if (x.items_per_cta != 1 && x.items_per_cta != 2 && x.items_per_cta != 4)
       return set_error(ctx, FCS_EINVAL, "class %d: items_per_cta %d not in {1,2,4}", c,
                        x.items_per_cta);
-    cfg.push_back(ClassCfg{L, x.thread_mult, x.items_per_cta});
+    cfg.push_back(ClassCfg{L, x.thread_mult, x.items_per_cta, x.engine});
   }
   int rc = ensure_batch_state(ctx);
   if (rc) return rc;
@@ -621,7 +631,7 @@ extern "C" int fcs_batch_plan_config(const fcs_batch_plan *plan, int *host_grain
   *host_ncfg = int(cls.size());
   if (host_grain) *host_grain = plan->grain;
   for (int c = 0; c < int(cls.size()) && c < max_cfg; ++c)
-    host_cfg[c] = fcs_batch_class_cfg{2 << cls[c].L, cls[c].ntm, cls[c].ipc, cls[c].nt};
+    host_cfg[c] = fcs_batch_class_cfg{2 << cls[c].L, cls[c].eng, cls[c].ntm, cls[c].ipc, cls[c].nt};
   return FCS_OK;
 }
 
@@ -687,7 +697,7 @@ extern "C" int fcs_batch_autotune(fcs_ctx *ctx, int nprob, const fcs_cp_problem 
   };
   // 1. ranks per item, every class at its default shape
   std::vector<ClassCfg> cfg;
-  for (int L : sizes) cfg.push_back(ClassCfg{L, 1, 1});
+  for (int L : sizes) cfg.push_back(ClassCfg{L, 1, 1, L == wdit::kL ? 1 : 0});
   int best = 1;
   float best_ms = 1e30f;
   for (int grain = 1; grain <= 64 && grain < 2 * rmax && rc == FCS_OK; grain *= 2) {
@@ -704,11 +714,20 @@ extern "C" int fcs_batch_autotune(fcs_ctx *ctx, int nprob, const fcs_cp_problem 
   for (auto c = cfg.rbegin(); c != cfg.rend() && rc == FCS_OK; ++c) {
     const ClassCfg keep = *c;
     ClassCfg bestc = keep;
-    for (int ntm : {1, 2}) {
-      if (ntm == 2 && c->L == wdit::kL) continue;
+    // shapes (engine, threads): slot FFT at 1 or 2 x the threads; for
+    // P = 8192 also the warp-DIT engine; P = 16384 has only warp-DIT
+    std::vector<std::pair<int, int>> shapes;
+    if (c->L == wdit::kL) {
+      shapes = {{1, 1}};
+    } else {
+      shapes = {{0, 1}, {0, 2}};
+      if (c->L == 12) shapes.push_back({1, 1});
+    }
+    for (const auto &sh : shapes) {
       for (int ipc : {1, 2, 4}) {
-        if (ntm == keep.ntm && ipc == keep.ipc) continue;
-        c->ntm = ntm;
+        if (sh.first == keep.eng && sh.second == keep.ntm && ipc == keep.ipc) continue;
+        c->eng = sh.first;
+        c->ntm = sh.second;
         c->ipc = ipc;
         float ms = 0.f;
         rc = timed(best, cfg, &ms);

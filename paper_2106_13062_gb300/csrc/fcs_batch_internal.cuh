@@ -8,12 +8,14 @@
 
 namespace fcs {
 
-// Tunable shape of one FFT-size class (log2 M = L): thread multiplier ntm
-// (1 or 2; the slot FFT runs M/16 or M/8 threads, at least a warp; fixed at
-// 1 for the P = 16384 engine) and items run one after another per CTA (ipc:
-// 1, 2 or 4).
+// Tunable shape of one FFT-size class (log2 M = L): the engine (for P = 8192
+// the slot FFT or the warp-DIT engine; P = 16384 always runs warp-DIT, the
+// other sizes the slot FFT), the slot FFT's thread multiplier ntm (1 or 2:
+// M/16 or M/8 threads, at least a warp) and items run one after another per
+// CTA (ipc: 1, 2 or 4).
 struct ClassCfg {
   int L, ntm, ipc;
+  int eng = 0;               // P = 8192: 0 = slot FFT, 1 = warp-DIT engine
 };
 
 // One launch of a batch: the items [first, first + count) of one FFT size.
@@ -22,7 +24,7 @@ struct BatchClass {
   int nt;                    // threads per CTA
   size_t smem;               // dynamic shared memory per CTA
   int first, count;
-  int L, ntm, ipc;           // the configuration it was built with
+  int L, ntm, ipc, eng;      // the configuration it was built with
 };
 
 // Layout of one batch in device memory (see batch_build).

@@ -64,7 +64,7 @@ __host__ __device__ constexpr int class_threads(int L, int ntm) {
 ClassKernel class_kernel_small(int L, int ntm, int ipc, int64_t Imax, int sb);  // L = 3 .. 9
 ClassKernel class_kernel_small2(int L, int ntm, int ipc, int64_t Imax, int sb); // L = 7 .. 9
 ClassKernel class_kernel_mid(int L, int ntm, int ipc, int64_t Imax, int sb);    // L = 10, 11
-ClassKernel class_kernel_12(int ntm, int ipc, int64_t Imax, int sb);            // L = 12
+ClassKernel class_kernel_12(int eng, int ntm, int ipc, int64_t Imax, int sb);   // L = 12
 ClassKernel class_kernel_13(int ipc, int64_t Imax, int sb);                     // L = 13
 
 // The kernels have internal linkage: each translation unit instantiates only
@@ -134,6 +134,35 @@ __global__ void __launch_bounds__(wdit::kNT) batch_class13_kernel(
     const int64_t r1 = min(P.R, r0 + P.rpi);
     const BatchView view{P, P.sb};
     cp13_run<CPT, RMAX>(view, w.y, r0, r1, unsigned(P.groups), smem_raw, tw, &is_last);
+  };
+  if constexpr (MULTI) {
+    const int first = blockIdx.x * ipc, last = min(count, first + ipc);
+    for (int it = first; it < last; ++it) {
+      if (it > first) __syncthreads();
+      one(it);
+    }
+  } else {
+    one(blockIdx.x);
+  }
+  pdl_wait_previous();
+}
+
+// The same for P = 8192 on the warp-DIT engine of wdit::w12 (256 threads,
+// two CTAs per SM; ra <= 32 RMAX).
+template <int CPT, int RMAX, bool MULTI>
+__global__ void __launch_bounds__(wdit::w12::kNT, 2) batch_class12w_kernel(
+    const BatchProb *__restrict__ probs, const int4 *__restrict__ items,
+    const float2 *__restrict__ tw, int count, int ipc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int is_last;
+  pdl_launch_dependents();
+  auto one = [&](int it) {
+    const int4 w = items[it];
+    const BatchProb &P = probs[w.x];
+    const int64_t r0 = int64_t(w.z) * P.rpi;
+    const int64_t r1 = min(P.R, r0 + P.rpi);
+    const BatchView view{P, P.sb};
+    cp12_run<CPT, RMAX>(view, w.y, r0, r1, unsigned(P.groups), smem_raw, tw, &is_last);
   };
   if constexpr (MULTI) {
     const int first = blockIdx.x * ipc, last = min(count, first + ipc);

@@ -559,8 +559,8 @@ __global__ void __launch_bounds__(wdit::kNT) cp15w_kernel(Cp15Args a, const floa
         }
         const bool more = rn < r1;
         if (more) fetch(rn, nn);
-        W::step1_row<RMAX, false, false>(A2 + warp * ra, ra, B + warp * wdit::kRS, tws, warp);
-        W::step1_row<RMAX, false, false>(A2 + (warp + 16) * ra, ra, B + (warp + 16) * wdit::kRS,
+        wdit::step1_row<RMAX, false, false>(A2 + warp * ra, ra, B + warp * wdit::kRS, tws, warp);
+        wdit::step1_row<RMAX, false, false>(A2 + (warp + 16) * ra, ra, B + (warp + 16) * wdit::kRS,
                                          tws, warp + 16);
         __syncthreads();
         // half the warps scatter the next column before step 2, half after
@@ -636,8 +636,8 @@ __global__ void __launch_bounds__(wdit::kNT) cp15w_kernel(Cp15Args a, const floa
         }
       }
       __syncthreads();
-      W::step1_row<16, true, true>(B + warp * wdit::kRS, 512, B + warp * wdit::kRS, tws, warp);
-      W::step1_row<16, true, true>(B + (warp + 16) * wdit::kRS, 512,
+      wdit::step1_row<16, true, true>(B + warp * wdit::kRS, 512, B + warp * wdit::kRS, tws, warp);
+      wdit::step1_row<16, true, true>(B + (warp + 16) * wdit::kRS, 512,
                                    B + (warp + 16) * wdit::kRS, tws, warp + 16);
       __syncthreads();
       float2 v[32];

@@ -90,6 +90,19 @@ __global__ void __launch_bounds__(wdit::kNT) cp13_kernel(CpArgs a, const float2 
   cp13_run<CPT, RMAX>(view, blockIdx.y, r0, r1, gridDim.x, smem_raw, tw, &is_last);
 }
 
+// The same for P = 8192 on the warp-DIT engine (256 threads, two CTAs per
+// SM).  RMAX = number of 32-entry blocks per scatter-buffer row.
+template <int CPT, int RMAX>
+__global__ void __launch_bounds__(wdit::w12::kNT, 2) cp12_kernel(CpArgs a,
+                                                                 const float2 *__restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int is_last;
+  const int64_t r0 = blockIdx.x * a.ranks_per_cta;
+  const int64_t r1 = min(a.R, r0 + a.ranks_per_cta);
+  const CpView view{a, a.sb};
+  cp12_run<CPT, RMAX>(view, blockIdx.y, r0, r1, gridDim.x, smem_raw, tw, &is_last);
+}
+
 // prep_kernel: in one launch, the factor transpose in 32 x 32 tiles,
 // UT[n][r][i] = U_n[i*ld + r] (times lambda_r for n = 0), and the clearing
 // of the spectrum accumulator and tickets.  256 threads per block.
@@ -164,10 +177,35 @@ int launch_cp13(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
   return check_cuda(ctx, e, "cp13_kernel");
 }
 
+template <int CPT>
+const void *cp12_pick_rmax(int ra) {
+  if (ra <= 128) return reinterpret_cast<const void *>(cp12_kernel<CPT, 4>);
+  if (ra <= 256) return reinterpret_cast<const void *>(cp12_kernel<CPT, 8>);
+  return reinterpret_cast<const void *>(cp12_kernel<CPT, 16>);
+}
+
+int launch_cp12(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
+  const int ra = (a.sb + 15) >> 4;
+  const size_t smem = Cp12Smem::bytes(ra);
+  const int cpt = int((Imax + wdit::w12::kNT - 1) / wdit::w12::kNT);
+  const void *kern = cpt <= 1 ? cp12_pick_rmax<1>(ra) : cpt <= 2 ? cp12_pick_rmax<2>(ra)
+                                                                 : cp12_pick_rmax<4>(ra);
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp12)");
+  const float2 *twp = ctx->twiddle;
+  void *args[] = {&a, &twp};
+  e = cudaLaunchKernel(kern, dim3(unsigned(groups), unsigned(a.D)), dim3(wdit::w12::kNT), args,
+                       smem, ctx->stream);
+  return check_cuda(ctx, e, "cp12_kernel");
+}
+
 template <int LOG2M>
 int launch_cp(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
   if constexpr (LOG2M == wdit::kL) {
     return launch_cp13(ctx, a, groups, Imax);
+  } else if constexpr (LOG2M == 12) {
+    return launch_cp12(ctx, a, groups, Imax);
   } else {
     constexpr int NT = fft_threads(LOG2M);
     const size_t smem = CpSmem<LOG2M, NT>::bytes(a.sb);
@@ -227,8 +265,10 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
   a.h = h;
   a.s = s;
   a.out = out;
-  // rank groups: about one CTA per SM over all sketches
-  int64_t groups = (int64_t(ctx->sm_count) + D - 1) / D;
+  // rank groups: about one CTA per SM over all sketches (two for P = 8192,
+  // whose engine fits two CTAs per SM)
+  const int64_t slots = int64_t(ctx->sm_count) * (log2m == 12 ? 2 : 1);
+  int64_t groups = (slots + D - 1) / D;
   if (groups < 1) groups = 1;
   if (groups > R) groups = R;
   a.ranks_per_cta = (R + groups - 1) / groups;

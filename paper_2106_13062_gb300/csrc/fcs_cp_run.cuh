@@ -404,4 +404,191 @@ __device__ __forceinline__ void cp13_run(const Prob &a, int d, int64_t r0, int64
   if (tid == 0) *ticket = 0u;
 }
 
+// Shared-memory layout of cp12_run; ra = number of float2 columns of the
+// 8-row scatter buffer.
+struct Cp12Smem {
+  static constexpr size_t kB = 0;                                   // 8 x kRS float2
+  static constexpr size_t kTw = kB + sizeof(float2) * 8 * wdit::kRS;
+  static constexpr size_t kA = kTw + sizeof(float2) * wdit::w12::kTwLen;
+  static size_t bytes(int ra) { return kA + sizeof(float2) * 8 * size_t(ra); }
+};
+
+// Ranks [r0, r1) of sketch d for P = 8192 on the warp-DIT engine of
+// wdit::w12 (256 threads): per transform the Count Sketch goes into an 8-row
+// scatter buffer, warp w runs the 512-point FFT of row w, one block barrier,
+// then each thread transforms its two columns and unpacks them in registers
+// (TWICE the spectrum values, so the inverse scales by 2^-N).  The mode
+// product and the rank sum stay in registers; the next column is scattered
+// between the barriers by half the warps before step 2 and half after.  CPT
+// and `groups` as for cp_run; RMAX = number of 32-entry blocks per
+// scatter-buffer row (ra <= 32 RMAX).  Every thread of the 256-thread block
+// calls it; it returns with no barrier pending.
+template <int CPT, int RMAX, class Prob>
+__device__ __forceinline__ void cp12_run(const Prob &a, int d, int64_t r0, int64_t r1,
+                                         unsigned groups, unsigned char *smem_raw,
+                                         const float2 *__restrict__ tw, int *is_last) {
+  namespace W = wdit::w12;
+  constexpr int NT = W::kNT, M = W::kM, HALF = M / 2;
+  float2 *B = reinterpret_cast<float2 *>(smem_raw + Cp12Smem::kB);
+  float2 *tws = reinterpret_cast<float2 *>(smem_raw + Cp12Smem::kTw);
+  float2 *A2 = reinterpret_cast<float2 *>(smem_raw + Cp12Smem::kA);
+  float *A = reinterpret_cast<float *>(A2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int N = a.modes();
+  const int sb = a.sb;
+  const int ra = (sb + 15) >> 4;
+  const int ua = W::ua_of(tid), ub = W::ub_of(tid);
+
+  float pv[CPT];
+  int ph[CPT];
+  auto fetch = [&](int64_t r, int n) {
+    const int64_t In = a.dim(n);
+    const float *col = a.column(n, r);
+    const int32_t *hn = a.hashes(d, n);
+    const int8_t *sn = a.signs(d, n);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int64_t i = tid + int64_t(c) * NT;
+      ph[c] = -1;
+      pv[c] = 0.f;
+      if (i < In) {
+        const float v = __ldg(col + i);
+        pv[c] = __ldg(sn + i) < 0 ? -v : v;
+        ph[c] = __ldg(hn + i);
+      }
+    }
+  };
+  auto scatter = [&](int64_t r, int n) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (unsigned(ph[c]) < unsigned(sb)) atomicAdd(A + W::a_index(ph[c], ra), pv[c]);
+    const int64_t In = a.dim(n);
+    if (In > int64_t(CPT) * NT) {
+      const float *col = a.column(n, r);
+      const int32_t *hn = a.hashes(d, n);
+      const int8_t *sn = a.signs(d, n);
+      for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
+        const int hb = __ldg(hn + i);
+        const float v = __ldg(col + i);
+        if (unsigned(hb) < unsigned(sb))
+          atomicAdd(A + W::a_index(hb, ra), __ldg(sn + i) < 0 ? -v : v);
+      }
+    }
+  };
+  fetch(r0, 0);
+  W::fill_twiddles(tws, tw);
+  for (int e = tid; e < 8 * ra; e += NT) A2[e] = make_float2(0.f, 0.f);
+  __syncthreads();
+  scatter(r0, 0);
+  __syncthreads();
+
+  float2 pa[8], pb[8], acca[8], accb[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acca[j] = accb[j] = make_float2(0.f, 0.f);
+  for (int64_t r = r0; r < r1; ++r) {
+    for (int n = 0; n < N; ++n) {
+      int64_t rn = r;
+      int nn = n + 1;
+      if (nn == N) {
+        nn = 0;
+        ++rn;
+      }
+      const bool more = rn < r1;
+      if (more) fetch(rn, nn);
+      wdit::step1_row<RMAX, false, false>(A2 + warp * ra, ra, B + warp * wdit::kRS, tws, warp);
+      __syncthreads();
+      const bool early = tid < NT / 2;
+      if (more && early) scatter(rn, nn);
+      float2 va[8], vb[8];
+      W::step2(B, tws, va, vb);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (n == 0) {
+          pa[j] = va[j];
+          pb[j] = vb[j];
+        } else {
+          pa[j] = cmul(pa[j], va[j]);
+          pb[j] = slot_mul(pb[j], vb[j], tid == 0 && j == 0);
+        }
+      }
+      if (n == N - 1) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          acca[j] = cadd(acca[j], pa[j]);
+          accb[j] = cadd(accb[j], pb[j]);
+        }
+      }
+      if (more && !early) scatter(rn, nn);
+      __syncthreads();
+    }
+  }
+
+  // publish the partial spectrum: bins ua + 512 j and ub + 512 j (thread 0:
+  // ub = 0, whose j = 0 value packs the real bins 0 and M)
+  float2 *Gd = a.spectrum() + d * int64_t(M + 2);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    atomicAdd(&Gd[ua + 512 * j], acca[j]);
+    if (tid == 0 && j == 0) {
+      atomicAdd(&Gd[0].x, accb[0].x);
+      atomicAdd(&Gd[M].x, accb[0].y);
+    } else {
+      atomicAdd(&Gd[ub + 512 * j], accb[j]);
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  unsigned *ticket = a.ticket(d);
+  if (tid == 0) *is_last = (atomicAdd(ticket, 1u) == groups - 1);
+  __syncthreads();
+  if (!*is_last) return;
+  __threadfence();
+
+  // last group for sketch d: the conj-packed sequence of the summed spectrum,
+  // row-swizzled into B, a forward complex FFT in place, conj and scaling
+  {
+    constexpr int PER = HALF / NT;
+    float2 Av[PER], Bv[PER], Wv[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int q = k * NT + tid;
+      if (q == 0) {
+        Av[k] = make_float2(__ldcg(&Gd[0].x), __ldcg(&Gd[M].x));
+        Bv[k] = __ldcg(&Gd[HALF]);
+        Wv[k] = make_float2(1.f, 0.f);
+      } else {
+        Av[k] = __ldcg(&Gd[q]);
+        Bv[k] = __ldcg(&Gd[M - q]);
+        Wv[k] = __ldg(&tw[q << (kLogTwN - 13)]);      // W_P^q, P = 8192
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int q = k * NT + tid;
+      float2 cq, cm;
+      pack_pair_conj_values_w(q, Av[k], Bv[k], Wv[k], cq, cm);
+      B[W::row_pos_swz(q)] = cq;
+      B[W::row_pos_swz(q ? M - q : HALF)] = cm;
+    }
+  }
+  __syncthreads();
+  wdit::step1_row<16, true, true>(B + warp * wdit::kRS, 512, B + warp * wdit::kRS, tws, warp);
+  __syncthreads();
+  float2 va[8], vb[8];
+  W::step2_complex(B, tws, va, vb);                  // Z[ua + 512 q1], Z[ub + 512 q1]
+  // 1/M of the inverse and 2^-N for the doubled unpack of every mode
+  const float sc = 1.0f / (float(M) * float(1 << N));
+  float *od = a.sketch(d);
+  const int64_t Jt = a.length();
+#pragma unroll
+  for (int q1 = 0; q1 < 8; ++q1) {
+    const int64_t ma = ua + 512 * q1, mb = ub + 512 * q1;
+    if (2 * ma < Jt) od[2 * ma] = va[q1].x * sc;
+    if (2 * ma + 1 < Jt) od[2 * ma + 1] = -va[q1].y * sc;
+    if (2 * mb < Jt) od[2 * mb] = vb[q1].x * sc;
+    if (2 * mb + 1 < Jt) od[2 * mb + 1] = -vb[q1].y * sc;
+  }
+  if (tid == 0) *ticket = 0u;
+}
+
 }  // namespace fcs

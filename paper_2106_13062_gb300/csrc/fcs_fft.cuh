@@ -668,58 +668,6 @@ __device__ __forceinline__ void step2(const float2 *B, const float2 *tws, float2
   }
 }
 
-// ---------------------------------------------------------------- M = 2^14
-// The same decomposition for M = 16384 (P = 32768): z[32 m2 + w] for 32
-// sub-sequences w of 512 points.  Step 1 runs the 512-point FFT of row w
-// exactly as above (each of the 16 warps takes rows w and w + 16); step 2
-// gives thread t column q2 = q2_of(t) of the 32 x 512 result, twiddles it by
-// W_M^(w q2) and takes a 32-point DFT over w, so that v[q1] = Z[q2 + 512 q1];
-// the real-FFT unpack pairs (q, M - q) again span lanes l and l ^ 16.
-namespace w15 {
-
-constexpr int kRows = 32;
-constexpr int kM = 1 << 14;
-constexpr int kTw2 = 16 * 32;               // after the step-1 table W512^(l ka)
-constexpr int kTwLen = kTw2 + 6 * kNT;      // W_M^(q2 2^b), b < 5; W_P^q2
-
-// Float index of real sample h in the 32-row scatter buffer (row m mod 32,
-// column m / 32 for m = h / 2; rows of ra float2).
-__device__ __forceinline__ int a_index(int h, int ra) {
-  const int m = h >> 1;
-  return 2 * ((m & 31) * ra + (m >> 5)) + (h & 1);
-}
-
-// Position of z[m] in a 32-row buffer of row stride kRS whose rows are
-// XOR-swizzled (row w holds z[32 m2 + w] at column m2 ^ w); read back by
-// step1_row<16, true, true>.
-__device__ __forceinline__ int row_pos_swz(int m) {
-  const int w = m & 31;
-  return w * kRS + ((m >> 5) ^ w);
-}
-
-// Per-CTA twiddle table: the step-1 part as in wdit::fill_twiddles, then for
-// thread t W_M^(q2(t) 2^b) at kTw2 + b*512 + t (b < 5) and W_P^q2(t) at
-// kTw2 + 5*512 + t, from tw[k] = exp(-2 pi i k / 2^15).  Called by all kNT
-// threads; every load is issued before the first store.
-__device__ __forceinline__ void fill_twiddles(float2 *tws, const float2 *__restrict__ tw) {
-  constexpr int PER = kTwLen / kNT;
-  static_assert(kTwLen % kNT == 0, "twiddle table fill");
-  float2 v[PER];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int e = threadIdx.x + k * kNT;
-    if (e < kTw2) {
-      const int ka = e >> 5, l = e & 31;
-      v[k] = __ldg(&tw[(l * ka) << (kLogTwN - 9)]);
-    } else {
-      const int b = (e - kTw2) >> 9, q2 = q2_of((e - kTw2) & (kNT - 1));
-      v[k] = b < 5 ? __ldg(&tw[(q2 << b) << (kLogTwN - 14)]) : __ldg(&tw[q2]);
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < PER; ++k) tws[threadIdx.x + k * kNT] = v[k];
-}
-
 // Step 1 for row w: the 512-point FFT of in_row (ra float2 entries; with SWZ
 // column c of row w sits at c ^ w) into out_row (kRS float2, also the
 // transpose scratch).  INPLACE: in_row == out_row, so the warp synchronises
@@ -772,6 +720,58 @@ __device__ __forceinline__ void step1_row(float2 *in_row, int ra, float2 *out_ro
   const int k0 = j + (odd ? 16 : 0);
 #pragma unroll
   for (int kk = 0; kk < 16; ++kk) T[k0 + 32 * kk] = v[kk];
+}
+
+// ---------------------------------------------------------------- M = 2^14
+// The same decomposition for M = 16384 (P = 32768): z[32 m2 + w] for 32
+// sub-sequences w of 512 points.  Step 1 runs the 512-point FFT of row w
+// exactly as above (each of the 16 warps takes rows w and w + 16); step 2
+// gives thread t column q2 = q2_of(t) of the 32 x 512 result, twiddles it by
+// W_M^(w q2) and takes a 32-point DFT over w, so that v[q1] = Z[q2 + 512 q1];
+// the real-FFT unpack pairs (q, M - q) again span lanes l and l ^ 16.
+namespace w15 {
+
+constexpr int kRows = 32;
+constexpr int kM = 1 << 14;
+constexpr int kTw2 = 16 * 32;               // after the step-1 table W512^(l ka)
+constexpr int kTwLen = kTw2 + 6 * kNT;      // W_M^(q2 2^b), b < 5; W_P^q2
+
+// Float index of real sample h in the 32-row scatter buffer (row m mod 32,
+// column m / 32 for m = h / 2; rows of ra float2).
+__device__ __forceinline__ int a_index(int h, int ra) {
+  const int m = h >> 1;
+  return 2 * ((m & 31) * ra + (m >> 5)) + (h & 1);
+}
+
+// Position of z[m] in a 32-row buffer of row stride kRS whose rows are
+// XOR-swizzled (row w holds z[32 m2 + w] at column m2 ^ w); read back by
+// step1_row<16, true, true>.
+__device__ __forceinline__ int row_pos_swz(int m) {
+  const int w = m & 31;
+  return w * kRS + ((m >> 5) ^ w);
+}
+
+// Per-CTA twiddle table: the step-1 part as in wdit::fill_twiddles, then for
+// thread t W_M^(q2(t) 2^b) at kTw2 + b*512 + t (b < 5) and W_P^q2(t) at
+// kTw2 + 5*512 + t, from tw[k] = exp(-2 pi i k / 2^15).  Called by all kNT
+// threads; every load is issued before the first store.
+__device__ __forceinline__ void fill_twiddles(float2 *tws, const float2 *__restrict__ tw) {
+  constexpr int PER = kTwLen / kNT;
+  static_assert(kTwLen % kNT == 0, "twiddle table fill");
+  float2 v[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int e = threadIdx.x + k * kNT;
+    if (e < kTw2) {
+      const int ka = e >> 5, l = e & 31;
+      v[k] = __ldg(&tw[(l * ka) << (kLogTwN - 9)]);
+    } else {
+      const int b = (e - kTw2) >> 9, q2 = q2_of((e - kTw2) & (kNT - 1));
+      v[k] = b < 5 ? __ldg(&tw[(q2 << b) << (kLogTwN - 14)]) : __ldg(&tw[q2]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) tws[threadIdx.x + k * kNT] = v[k];
 }
 
 // Step 2 up to the complex spectrum: v[q1] = Z[q2 + 512 q1], q2 = q2_of(t).
@@ -828,6 +828,119 @@ __device__ __forceinline__ void step2(const float2 *B, const float2 *tws, float2
 }
 
 }  // namespace w15
+
+// ---------------------------------------------------------------- M = 2^12
+// M = 4096 (P = 8192) on 256 threads: z[8 m2 + w] for 8 sub-sequences of
+// 512 points, warp w running step 1 on row w (step1_row).  In step 2 thread t
+// takes the two columns ua(t) and ub(t) = 512 - ua(t) (t = 0: columns 256
+// and 0), twiddles each by W_M^(w q2), takes two 8-point DFTs, and does the
+// real-FFT unpack inside the thread: bin ua + 512 q1 pairs with
+// ub + 512 (7 - q1), so no data crosses lanes.
+namespace w12 {
+
+constexpr int kRows = 8;
+constexpr int kM = 1 << 12;
+constexpr int kNT = 256;
+constexpr int kTw2 = 16 * 32;               // after the step-1 table W512^(l ka)
+constexpr int kTwLen = kTw2 + 7 * kNT;      // W_M^(ua 2^b), W_M^(ub 2^b) (b < 3), W_P^ua
+
+__device__ __forceinline__ int ua_of(int t) { return t ? t : 256; }
+__device__ __forceinline__ int ub_of(int t) { return t ? 512 - t : 0; }
+
+// Float index of real sample h in the 8-row scatter buffer (row m mod 8,
+// column m / 8 for m = h / 2; rows of ra float2).
+__device__ __forceinline__ int a_index(int h, int ra) {
+  const int m = h >> 1;
+  return 2 * ((m & 7) * ra + (m >> 3)) + (h & 1);
+}
+
+// Position of z[m] in an 8-row buffer of row stride kRS, rows XOR-swizzled
+// (row w holds z[8 m2 + w] at column m2 ^ w), read back by
+// step1_row<16, true, true>.
+__device__ __forceinline__ int row_pos_swz(int m) {
+  const int w = m & 7;
+  return w * kRS + ((m >> 3) ^ w);
+}
+
+// Per-CTA twiddle table: the step-1 part (W512^(l ka) at ka*32 + l), then for
+// thread t W_M^(ua 2^b) at kTw2 + b*256 + t, W_M^(ub 2^b) at
+// kTw2 + (3 + b)*256 + t (b < 3) and W_P^ua at kTw2 + 6*256 + t, from
+// tw[k] = exp(-2 pi i k / 2^15).  Every load is issued before the first store.
+__device__ __forceinline__ void fill_twiddles(float2 *tws, const float2 *__restrict__ tw) {
+  constexpr int PER = kTwLen / kNT;
+  static_assert(kTwLen % kNT == 0, "twiddle table fill");
+  float2 v[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int e = threadIdx.x + k * kNT;
+    if (e < kTw2) {
+      const int ka = e >> 5, l = e & 31;
+      v[k] = __ldg(&tw[(l * ka) << (kLogTwN - 9)]);
+    } else {
+      const int b = (e - kTw2) >> 8, t = (e - kTw2) & (kNT - 1);
+      const int ua = ua_of(t), ub = ub_of(t);
+      v[k] = b < 3   ? __ldg(&tw[(ua << b) << (kLogTwN - 12)])
+             : b < 6 ? __ldg(&tw[(ub << (b - 3)) << (kLogTwN - 12)])
+                     : __ldg(&tw[ua << (kLogTwN - 13)]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) tws[threadIdx.x + k * kNT] = v[k];
+}
+
+// Step 2 up to the complex spectrum: va[q1] = Z[ua + 512 q1],
+// vb[q1] = Z[ub + 512 q1].
+__device__ __forceinline__ void step2_complex(const float2 *B, const float2 *tws, float2 (&va)[8],
+                                              float2 (&vb)[8]) {
+  const int t = threadIdx.x;
+  const int ua = ua_of(t), ub = ub_of(t);
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    va[w] = B[w * kRS + ua];
+    vb[w] = B[w * kRS + ub];
+  }
+  float2 wa[3], wb[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    wa[b] = tws[kTw2 + b * kNT + t];
+    wb[b] = tws[kTw2 + (3 + b) * kNT + t];
+  }
+  twiddle_powers<3>(va, wa);
+  twiddle_powers<3>(vb, wb);
+  Dft<8>::run(va);
+  Dft<8>::run(vb);
+}
+
+// Step 2 with the real-FFT unpack: TWICE the half-spectrum values,
+// va[q1] = 2 X[ua + 512 q1], vb[q1] = 2 X[ub + 512 q1]; for thread 0 (ub = 0)
+// vb[0] packs the two real bins (2 X[0], 2 X[M]).
+__device__ __forceinline__ void step2(const float2 *B, const float2 *tws, float2 (&va)[8],
+                                      float2 (&vb)[8]) {
+  const int t = threadIdx.x;
+  step2_complex(B, tws, va, vb);
+  if (t != 0) {
+    const float2 wP = tws[kTw2 + 6 * kNT + t];      // W_P^ua, P = 8192
+#pragma unroll
+    for (int q1 = 0; q1 < 8; ++q1) {
+      // W_P^(ua + 512 q1) = W_P^ua exp(-2 pi i q1 / 16); partner ub + 512 (7 - q1)
+      const float2 wq = q1 == 0 ? wP : cmul(wP, unit64(4 * q1));
+      unpack2_twice(va[q1], vb[7 - q1], wq, va[q1], vb[7 - q1]);
+    }
+  } else {
+    // column 256 pairs with itself: 256 + 512 q1 <-> 256 + 512 (7 - q1)
+#pragma unroll
+    for (int q1 = 0; q1 < 4; ++q1)
+      unpack2_twice(va[q1], va[7 - q1], unit64(2 + 4 * q1), va[q1], va[7 - q1]);
+    // column 0: 512 q1 <-> 512 (8 - q1); q1 = 0 and 4 pair with themselves
+    const float2 z0 = vb[0], z4 = vb[4];
+    vb[0] = make_float2(2.f * (z0.x + z0.y), 2.f * (z0.x - z0.y));
+    vb[4] = make_float2(2.f * z4.x, -2.f * z4.y);
+#pragma unroll
+    for (int q1 = 1; q1 < 4; ++q1) unpack2_twice(vb[q1], vb[8 - q1], unit64(4 * q1), vb[q1], vb[8 - q1]);
+  }
+}
+
+}  // namespace w12
 
 }  // namespace wdit
 

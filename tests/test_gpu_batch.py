@@ -25,6 +25,8 @@ SHAPES = [
     ([200, 150, 300], [5000, 5000, 5000], 7, 4),
     ([90, 70, 80], [1500, 1200, 1000], 33, 5),
     ([1000, 700], [2000, 3000], 64, 10),
+    ([100, 90, 80, 70], [1100, 1200, 1000, 1100], 6, 3),   # P = 8192, short hash ranges
+    ([1500, 40], [5000, 1000], 5, 2),                 # P = 8192, long ranges, a mode > 4 x 256
 ]
 
 
@@ -164,23 +166,30 @@ def test_plan_outliving_its_context(fcs):
     assert not plan._h.value
 
 
-CLASS_SHAPES = [(1, 1), (2, 1), (1, 2), (2, 2), (1, 4), (2, 4)]
+# (engine for P = 8192, thread multiplier of the slot FFT, items per CTA)
+CLASS_SHAPES = [(0, 1, 1), (0, 2, 1), (0, 1, 2), (0, 2, 2), (0, 1, 4), (0, 2, 4),
+                (1, 1, 1), (1, 1, 2), (1, 1, 4)]
 
 
-@pytest.mark.parametrize("ntm,ipc", CLASS_SHAPES)
-def test_every_class_shape_matches_single_calls(fcs, ctx, ntm, ipc):
-    """Each thread multiplier and items-per-CTA count the autotuner may pick,
-    applied to every FFT-length class of the batch (P = 16 ... 16384; the
-    P = 16384 engine takes thread multiplier 1 only), gives each problem's
+@pytest.mark.parametrize("eng,ntm,ipc", CLASS_SHAPES)
+def test_every_class_shape_matches_single_calls(fcs, ctx, eng, ntm, ipc):
+    """Each engine, thread multiplier and items-per-CTA count the autotuner
+    may pick, applied to every FFT-length class of the batch (P = 16 ...
+    16384: the warp-DIT engine is an option at P = 8192 and the only engine at
+    P = 16384, the slot FFT runs the other sizes), gives each problem's
     fcs_sketch_cp result."""
     probs, refs, keep = _make(fcs, ctx, seed=21)
     lens = sorted({1 << max(4, (sum(J) - len(J)).bit_length()) for _, _, _, _, _, _, _, _, J
                    in keep}, reverse=True)
-    classes = [(P, ntm if P < 16384 else 1, ipc) for P in lens]
+    assert 8192 in lens and 16384 in lens
+    classes = []
+    for P in lens:
+        e = 1 if P == 16384 else (eng if P == 8192 else 0)
+        classes.append((P, ntm if e == 0 else 1, ipc, e))
     plan = fcs.BatchPlan(ctx, probs, grain=2, classes=classes)
     grain, got = plan.config()
     assert grain == 2
-    assert [(p, t, i) for p, t, i, _ in got] == classes
+    assert [(p, t, i, e) for p, t, i, _, e in got] == classes
     plan.launch()
     torch.cuda.synchronize()
     for k, ref in enumerate(refs):
@@ -222,15 +231,15 @@ def test_autotuner_picks_class_shapes(fcs, tmp_path):
             plan = fcs.BatchPlan(c, probs)               # grain 0: the tuned entry
             grain, cls = plan.config()
             assert grain == g and len(cls) == 1
-            P, ntm, ipc, nt = cls[0]
-            assert ntm in (1, 2) and ipc in (1, 2, 4) and nt >= 32
+            P, ntm, ipc, nt, eng = cls[0]
+            assert ntm in (1, 2) and ipc in (1, 2, 4) and nt >= 32 and eng == 0
             # the cache file holds the same choice
             stored = {}
             for line in open(path):
                 tok = line.split()
                 stored[int(tok[1])] = stored.get(int(tok[1]), []) + [tuple(
                     int(x) for x in t.split(":")) for t in tok[2:]]
-            assert any((P.bit_length() - 2, ntm, ipc) in v for v in stored.values())
+            assert any((P.bit_length() - 2, ntm, ipc, eng) in v for v in stored.values())
             plan.launch()
             torch.cuda.synchronize()
             for k, ref in enumerate(refs):

@@ -171,6 +171,15 @@ def test_cp_tiny_and_dense_agree(fcs, ctx, orc):
     ([50, 60, 70], [8192, 4096, 2048], 2, 16, {}),
     ([100], [16384], 2, 1, {}),
     ([200, 150, 100, 120], [4000, 4000, 4000, 4000], 3, 2, {}),   # 4-row scatter buffer
+    # P = 8192 (warp-DIT engine of 256 threads, 8-row scatter buffer): order 1
+    # with a tail beyond the prefetch, orders 2 and 4, D = 16 with few ranks,
+    # J = P, and the shortest scatter-buffer rows
+    ([3000], [6000], 3, 2, {}),
+    ([700, 900], [4000, 3000], 6, 3, {"lam_none": True}),
+    ([40, 700, 30, 1200], [2000, 2000, 1000, 2000], 4, 2, {"ld_pad": 3}),
+    ([50, 60, 70], [4096, 2048, 1024], 2, 16, {}),
+    ([100], [8192], 2, 1, {}),
+    ([200, 150, 100, 120], [1500, 1500, 1500, 1500], 5, 2, {}),
 ])
 def test_cp_shapes(fcs, ctx, orc, I, J, R, D, kw):
     _cp_case(fcs, ctx, orc, I, J, R, D, 21, **kw)
