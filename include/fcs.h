@@ -269,8 +269,8 @@ int fcs_batch_sketch_cp(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_prob
 
 /* Shape of one FFT-length class of a batch plan.  engine: 0 = the slot FFT
  * (Stockham passes in shared memory, P <= 8192), 1 = the warp-DIT engine
- * (512-point sub-FFTs per warp, then a column step per thread; P = 8192 and
- * P = 16384, the only engine there).  thread_mult (slot FFT only): 1 = one
+ * (512-point sub-FFTs per warp, then a column step per thread; P = 8192, where
+ * it is the default, and P = 16384, the only engine there).  thread_mult (slot FFT only): 1 = one
  * radix-16 butterfly per thread (P/32 threads, at least 32), 2 = twice as
  * many threads.  items_per_cta: 1, 2 or 4 work items run one after another by
  * each CTA.  threads: the block size that results (output of
@@ -284,8 +284,8 @@ typedef struct fcs_batch_class_cfg {
 } fcs_batch_class_cfg;
 
 /* fcs_batch_plan_create with explicit class shapes (classes not listed take
- * the slot FFT -- warp-DIT for P = 16384 -- with thread_mult = 1 and
- * items_per_cta = 1) and grain (0 = the default grain). */
+ * the warp-DIT engine at P = 8192 and 16384, the slot FFT below, with
+ * thread_mult = 1 and items_per_cta = 1) and grain (0 = the default grain). */
 int fcs_batch_plan_create_cfg(fcs_ctx *ctx, int nprob, const fcs_cp_problem *host_probs,
                               int grain, int ncfg, const fcs_batch_class_cfg *host_cfg,
                               fcs_batch_plan **plan);

@@ -771,7 +771,7 @@ class BatchPlan:
     def __init__(self, ctx: Context, problems, grain: int = 0, classes=None):
         """classes: None (autotuned or default shapes) or a list of
         (fft_len, thread_mult, items_per_cta[, engine]) per FFT-length class;
-        engine 0 = slot FFT, 1 = warp-DIT (default: 1 for P = 16384, else 0)."""
+        engine 0 = slot FFT, 1 = warp-DIT (default: 1 for P = 8192 and 16384, else 0)."""
         self.ctx = ctx
         self._arr = _problem_array(problems)
         h = C.c_void_p()
@@ -782,7 +782,7 @@ class BatchPlan:
         else:
             def one(c):
                 p, t, i = (int(x) for x in c[:3])
-                e = int(c[3]) if len(c) > 3 else (1 if p == 16384 else 0)
+                e = int(c[3]) if len(c) > 3 else (1 if p in (8192, 16384) else 0)
                 return BatchClassCfg(p, e, t, i, 0)
             cfg = (BatchClassCfg * max(1, len(classes)))(*[one(c) for c in classes])
             ctx.check(lib().fcs_batch_plan_create_cfg(ctx.handle, len(problems), self._arr,

@@ -93,8 +93,13 @@ __global__ void batch_transpose_kernel(const TransposeTask *__restrict__ tasks, 
   }
 }
 
-// Class kernel for log2 M = L at thread multiplier ntm (slot FFT only; the
-// P = 16384 engine has one thread count) running ipc items per CTA.
+// Engine of a class without a tuned or explicit shape: the warp-DIT engines
+// where they exist (P = 8192 and 16384), the slot FFT below.
+int default_engine(int L) { return (L == wdit::kL || L == 12) ? 1 : 0; }
+
+// Class kernel for log2 M = L with engine eng, at thread multiplier ntm (slot
+// FFT only; the warp-DIT engines have one thread count) running ipc items
+// per CTA.
 ClassKernel class_kernel(int L, int eng, int ntm, int ipc, int64_t Imax, int sb) {
   if (L == wdit::kL) return class_kernel_13(ipc, Imax, sb);
   if (L == 12) return class_kernel_12(eng, ntm, ipc, Imax, sb);
@@ -333,7 +338,7 @@ int batch_build(fcs_ctx *ctx, int nprob, const fcs_cp_problem *q, int grain, cha
       Imax = std::max(Imax, hp[items[j].x].Imax);
       sb = std::max(sb, hp[items[j].x].sb);
     }
-    ClassCfg c{L, 1, 1, L == wdit::kL ? 1 : 0};
+    ClassCfg c{L, 1, 1, default_engine(L)};
     if (cfg)
       for (const ClassCfg &x : *cfg)
         if (x.L == L) c = x;
@@ -697,7 +702,7 @@ extern "C" int fcs_batch_autotune(fcs_ctx *ctx, int nprob, const fcs_cp_problem 
   };
   // 1. ranks per item, every class at its default shape
   std::vector<ClassCfg> cfg;
-  for (int L : sizes) cfg.push_back(ClassCfg{L, 1, 1, L == wdit::kL ? 1 : 0});
+  for (int L : sizes) cfg.push_back(ClassCfg{L, 1, 1, default_engine(L)});
   int best = 1;
   float best_ms = 1e30f;
   for (int grain = 1; grain <= 64 && grain < 2 * rmax && rc == FCS_OK; grain *= 2) {
