@@ -497,16 +497,29 @@ int plan_create(fcs_ctx *ctx, int nprob_all, const fcs_cp_problem *q_all, int gr
 int plan_launch(fcs_ctx *ctx, const fcs_batch_plan *plan) {
   if (ctx->spec_cache)
     for (const auto &o : plan->outs) spec_cache_invalidate(ctx, o.first, o.second);
+  // The first long problem on the P = 2^15 warp-DIT route has its accumulator
+  // cleared before the chain and its kernel launched as a programmatic
+  // dependent of the chain's last class, so its CTAs take the SMs the chain
+  // frees while it drains.  The other long problems share the scratch and
+  // run one after another afterwards.
+  bool split = false;
+  auto long_call = [&](const fcs_cp_problem &p, int stage, bool *sp) -> int {
+    Modes m{};
+    int rc = make_modes(ctx, p.N, p.I, p.J, p.ldh, &m);
+    if (rc) return rc;
+    return big_sketch_cp(ctx, m, p.R, p.D, p.U, p.ldU, p.lambda, p.h, p.s, p.out,
+                         ilog2_ceil(m.Jt), plan->long_ws, plan->long_bytes, stage, sp);
+  };
+  if (plan->dev && !plan->longp.empty()) {
+    int rc = long_call(plan->longp[0], 1, &split);
+    if (rc) return rc;
+  }
   if (plan->dev) {
     int rc = batch_issue(ctx, static_cast<char *>(plan->dev), plan->build);
     if (rc) return rc;
   }
-  for (const fcs_cp_problem &p : plan->longp) {
-    Modes m{};
-    int rc = make_modes(ctx, p.N, p.I, p.J, p.ldh, &m);
-    if (rc) return rc;
-    rc = big_sketch_cp(ctx, m, p.R, p.D, p.U, p.ldU, p.lambda, p.h, p.s, p.out,
-                       ilog2_ceil(m.Jt), plan->long_ws, plan->long_bytes);
+  for (size_t k = 0; k < plan->longp.size(); ++k) {
+    int rc = long_call(plan->longp[k], k == 0 && split ? 2 : 0, nullptr);
     if (rc) return rc;
   }
   return FCS_OK;

@@ -656,6 +656,9 @@ __global__ void __launch_bounds__(wdit::kNT) cp15w_kernel(Cp15Args a, const floa
     }
     __syncthreads();                                  // B is reused by the next item
   }
+  // launched as a programmatic dependent (after a batch chain), complete only
+  // after the preceding grid; otherwise this returns at once
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ---------------------------------------------------------------- contractions
@@ -865,7 +868,9 @@ size_t big_sketch_cp_bytes(const Modes &m, int64_t R, int D, int log2p, size_t c
 
 int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *const *host_U,
                   const int64_t *host_ldU, const float *lambda, const int32_t *h,
-                  const int8_t *s, float *out, int log2p, void *ext_ws, size_t ext_bytes) {
+                  const int8_t *s, float *out, int log2p, void *ext_ws, size_t ext_bytes,
+                  int stage, bool *split) {
+  if (split) *split = false;
   const int L1 = log2p - 1 - kL2;
   const int64_t M = int64_t(1) << (log2p - 1), P = 2 * M;
   const int N = m.N;
@@ -896,14 +901,22 @@ int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *c
       a.ticket = reinterpret_cast<unsigned *>(a.G + size_t(D) * size_t(M + 1));
       a.prod = reinterpret_cast<float4 *>(static_cast<char *>(ws) + f.gbytes);
       a.out = out;
-      int rc = check_cuda(ctx, cudaMemsetAsync(ws, 0, f.gbytes, ctx->stream), "cudaMemsetAsync(G)");
-      if (rc) return rc;
       int64_t jmax = 1, imax = 1;
       for (int n = 0; n < N; ++n) {
         jmax = std::max<int64_t>(jmax, m.J[n]);
         imax = std::max<int64_t>(imax, m.I[n]);
       }
       const int ra = int((jmax + 63) >> 6);
+      if (stage != 0 && ra > kRaMax15) return FCS_OK;     // not split: stage 0 runs it
+      if (stage != 2) {
+        int rc = check_cuda(ctx, cudaMemsetAsync(ws, 0, f.gbytes, ctx->stream),
+                            "cudaMemsetAsync(G)");
+        if (rc) return rc;
+      }
+      if (stage == 1) {
+        if (split) *split = true;
+        return FCS_OK;
+      }
       if (ra <= kRaMax15) {
         // the warp-DIT engine: scatter buffer of 32 rows of ra float2
         const int cpt = int((imax + wdit::kNT - 1) / wdit::kNT);
@@ -923,10 +936,20 @@ int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *c
         const float2 *twp = ctx->twiddle;
         int rap = ra;
         void *args[] = {&a, &twp, &rap};
-        e = cudaLaunchKernel(kern, dim3(unsigned(f.ctas)), dim3(wdit::kNT), args, smem,
-                             ctx->stream);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(f.ctas));
+        cfg.blockDim = dim3(wdit::kNT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = ctx->stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = stage == 2 ? 1 : 0;
+        e = cudaLaunchKernelExC(&cfg, kern, args);
         return check_cuda(ctx, e, "cp15w_kernel");
       }
+      // the block-FFT kernel (stage 0 only; G was cleared above)
       const size_t smem = sizeof(float2) * padded_len(kM2);
       cudaError_t e = cudaFuncSetAttribute(cp15_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            int(smem));
@@ -935,6 +958,7 @@ int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *c
       return check_cuda(ctx, cudaGetLastError(), "cp15_kernel");
     }
   }
+  if (stage != 0) return FCS_OK;                       // not split: stage 0 runs it
   int64_t tc;
   size_t need;
   big_cp_plan(m, R, D, log2p, cap, &tc, &need);

@@ -496,11 +496,15 @@ int make_modes_msg(char *err, size_t n, int N, const int64_t *host_I,
 // FFT-based calls for kMaxLog2P < log2p <= kMaxLog2PBig (fcs_big.cu); the
 // callers have validated the arguments.
 // ext_ws: caller-owned device buffer of ext_bytes (a batch plan's), or NULL
-// for the context workspace.
+// for the context workspace.  stage 0 issues everything.  A batch plan splits
+// the P = 2^15 warp-DIT route in two: stage 1 issues only the clearing of its
+// accumulator (*split = true when the route applies; otherwise nothing is
+// issued), stage 2 only its kernel, launched as a programmatic dependent of
+// the kernel before it in the stream (it waits for that grid at its end).
 int big_sketch_cp(fcs_ctx *ctx, const Modes &m, int64_t R, int D, const float *const *host_U,
                   const int64_t *host_ldU, const float *lambda, const int32_t *h,
                   const int8_t *s, float *out, int log2p, void *ext_ws = nullptr,
-                  size_t ext_bytes = 0);
+                  size_t ext_bytes = 0, int stage = 0, bool *split = nullptr);
 // Device bytes big_sketch_cp uses when its buffer holds at most `cap` bytes.
 size_t big_sketch_cp_bytes(const Modes &m, int64_t R, int D, int log2p, size_t cap, int nsm);
 int big_contract(fcs_ctx *ctx, const Modes &m, int kind, int free_mode, int D,

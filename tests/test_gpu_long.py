@@ -163,6 +163,55 @@ def test_batch_mixes_long_and_short(fcs, ctx, orc):
         assert_sketch_close(host(out), ref)
 
 
+def test_batch_two_long_problems_linked_and_replayed(fcs, ctx, orc):
+    """Two P = 2^15 problems in one plan with short ones: the first long
+    problem is linked after the chain's last class (its CTAs start while the
+    chain drains), the second follows it on the same scratch.  Both the plain
+    launch and a captured replay after the factors change in place must give
+    the oracle's sketches."""
+    shapes = [([100, 120, 90], [3000, 2000, 1000], 7, 3),       # P = 8192
+              ([80, 90, 70], [9000, 8000, 7000], 5, 2),         # P = 2^15, linked
+              ([60, 70, 50], [8000, 9000, 6000], 3, 3),         # P = 2^15, after it
+              ([60, 50], [700, 900], 4, 4)]                     # P = 2048
+    probs, keep, host_in = [], [], []
+    for k, (I, J, R, D) in enumerate(shapes):
+        U, lam = synth.cp_factors(80 + k, I, R)
+        ho, so = orc.make_hashes(90 + k, I, J, D)
+        dev = [cuda(u) for u in U] + [cuda(lam), cuda(ho), cuda(so)]
+        p, out = fcs.cp_problem(dev[:len(U)], dev[-3], J, dev[-2], dev[-1])
+        probs.append(p)
+        keep.append((dev, out))
+        host_in.append((U, lam, J, ho, so))
+
+    def refs(scale):
+        return [orc.fcs_cp([u.astype(np.float64) * (scale if n == 0 else 1.0)
+                            for n, u in enumerate(U)], lam.astype(np.float64), J, ho, so)
+                for U, lam, J, ho, so in host_in]
+
+    plan = fcs.BatchPlan(ctx, probs)
+    plan.launch()
+    torch.cuda.synchronize()
+    for k, ((_, out), ref) in enumerate(zip(keep, refs(1.0))):
+        assert_sketch_close(host(out), ref, what=f"plain launch, problem {k}")
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        plan.launch()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=st):
+            plan.launch()
+    torch.cuda.current_stream().wait_stream(st)
+    for dev, out in keep:
+        dev[0].mul_(-1.5)                                # mode-1 factor, in place
+        out.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    for k, ((_, out), ref) in enumerate(zip(keep, refs(-1.5))):
+        assert_sketch_close(host(out), ref, what=f"graph replay, problem {k}")
+    plan.close()
+
+
 def test_server_long_request(fcs, ctx, orc):
     I, J, R, D = [120, 100, 90], [9000, 8000, 7000], 6, 2       # P = 2^15
     U, lam = synth.cp_factors(70, I, R)
