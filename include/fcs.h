@@ -160,6 +160,23 @@ int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
                   int64_t ldh, float *out);
 
 /*
+ * fcs_sketch_cp_seeded -- fcs_make_hashes followed by fcs_sketch_cp in one
+ * call: the hash tables of `seed` (bit for bit as fcs_make_hashes writes
+ * them) go to h [D][sum I] int32 and s [D][sum I] int8 (device, densely
+ * packed; the caller keeps them for contractions and recovery), and the
+ * sketch of [[lambda; U_1..U_N]] to out [D][Jt], as fcs_sketch_cp with
+ * those tables.  For P <= 16384 the tables are written by the same launch
+ * that transposes the factors, so the call issues two kernels instead of
+ * three; longer transforms generate them with their own launch first.
+ * Arguments, workspace and errors otherwise as fcs_sketch_cp (and I_n <= 2^32
+ * as fcs_make_hashes).
+ */
+int fcs_sketch_cp_seeded(fcs_ctx *ctx, uint64_t seed, int N, const int64_t *host_I,
+                         const int32_t *host_J, int64_t R, int D,
+                         const float *const *host_U, const int64_t *host_ldU,
+                         const float *lambda, int32_t *h, int8_t *s, float *out);
+
+/*
  * fcs_sketch_cp_host -- fcs_sketch_cp from and to HOST memory, with the hash
  * tables generated from `seed` (as fcs_make_hashes would, bit for bit).
  *   host_U[N]: HOST pointers, U_n is I_n x R FP32 row-major with leading
@@ -169,8 +186,9 @@ int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
  * factors and lambda (ranges that follow each other in host memory move in
  * one copy; pinned memory makes them asynchronous), the hash generation, the
  * sketch, and the device-to-host copy of the result, which is complete once
- * the stream has been synchronised.  The inputs must stay unchanged until
- * then.  Device staging of 4*(sum_n I_n*R + R) + 5*D*sum_n I_n + 4*D*Jt bytes
+ * the stream has been synchronised (the hash generation runs in the factor
+ * transpose launch, as in fcs_sketch_cp_seeded).  The inputs must stay
+ * unchanged until then.  Device staging of 4*(sum_n I_n*R + R) + 5*D*sum_n I_n + 4*D*Jt bytes
  * (each part rounded up to 256) is held by the context (within its budget,
  * beside the workspace fcs_sketch_cp uses).
  */

@@ -73,6 +73,9 @@ def lib() -> C.CDLL:
                 "fcs_sketch_cp": (C.c_int, [vp, C.c_int, i64p, i32p, C.c_int64,
                                             C.c_int, C.POINTER(C.c_void_p), i64p,
                                             vp, vp, vp, C.c_int64, vp]),
+                "fcs_sketch_cp_seeded": (C.c_int, [vp, C.c_uint64, C.c_int, i64p, i32p,
+                                                   C.c_int64, C.c_int, C.POINTER(C.c_void_p),
+                                                   i64p, vp, vp, vp, vp]),
                 "fcs_sketch_cp_host": (C.c_int, [vp, C.c_int, i64p, i32p, C.c_int64,
                                                  C.c_int, C.POINTER(C.c_void_p), i64p,
                                                  vp, C.c_uint64, vp]),
@@ -203,7 +206,8 @@ def exported_symbols():
     """Names of the C entry points this binding expects libfcs.so to export."""
     return ["fcs_version", "fcs_create", "fcs_destroy", "fcs_set_stream",
             "fcs_last_error", "fcs_workspace_bytes", "fcs_make_hashes",
-            "fcs_sketch_dense", "fcs_sketch_cp", "fcs_sketch_cp_noalloc", "fcs_sketch_cp_host",
+            "fcs_sketch_dense", "fcs_sketch_cp", "fcs_sketch_cp_seeded", "fcs_sketch_cp_noalloc",
+            "fcs_sketch_cp_host",
             "fcs_contract", "fcs_contract_both", "fcs_cache_spectra", "fcs_forget",
             "fcs_fold", "fcs_sketch_inner", "fcs_rtpm", "fcs_als",
             "fcs_recover", "fcs_sketch_outer", "fcs_sketch_outer_sum",
@@ -432,6 +436,39 @@ def fcs_sketch_cp(ctx: Context, U, lam, J, h, s, ldh: int = 0,
         _arr(C.c_int32, J), R, D, ptrs, _arr(C.c_int64, [u.stride(0) for u in U]),
         _ptr(lam), _ptr(h), _ptr(s), ldh, _ptr(out)))
     return out
+
+
+def fcs_sketch_cp_seeded(ctx: Context, U, lam, J, D: int, seed: int,
+                         out: torch.Tensor | None = None, h: torch.Tensor | None = None,
+                         s: torch.Tensor | None = None):
+    """fcs_make_hashes + fcs_sketch_cp in one call (fcs_sketch_cp_seeded): the
+    hash tables of `seed` go to h (int32) and s (int8), both [D, sum I] and
+    densely packed (allocated here unless given), and the sketch of
+    [[lam; U_1..U_N]] to out [D, Jt].  Returns (out, h, s)."""
+    ctx._sync_stream()
+    if not U:
+        raise ValueError("need at least one factor matrix")
+    I = [int(u.shape[0]) for u in U]
+    tot = sum(I)
+    dev = U[0].device
+    if h is None:
+        h = torch.empty((int(D), tot), dtype=torch.int32, device=dev)
+    if s is None:
+        s = torch.empty((int(D), tot), dtype=torch.int8, device=dev)
+    _need(h, torch.int32, "h")
+    _need(s, torch.int8, "s")
+    if tuple(h.shape) != (int(D), tot) or tuple(s.shape) != (int(D), tot):
+        raise ValueError("h and s must be [D, sum I] (densely packed tables)")
+    N, R = _check_cp(U, lam, J, h, s, out)
+    Jt = jtilde(J)
+    if out is None:
+        out = torch.empty((int(D), Jt), dtype=torch.float32, device=dev)
+    ptrs = (C.c_void_p * N)(*[u.data_ptr() for u in U])
+    ctx.check(lib().fcs_sketch_cp_seeded(
+        ctx.handle, C.c_uint64(int(seed)), N, _arr(C.c_int64, I), _arr(C.c_int32, J), R,
+        int(D), ptrs, _arr(C.c_int64, [u.stride(0) for u in U]), _ptr(lam), _ptr(h), _ptr(s),
+        _ptr(out)))
+    return out, h, s
 
 
 def fcs_sketch_cp_host(ctx: Context, U, lam, J, D: int, seed: int,

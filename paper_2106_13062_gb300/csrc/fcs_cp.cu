@@ -4,8 +4,9 @@
 // convolution, so out = the first Jt samples).
 //
 // Two kernels.  (1) prep_kernel writes the factor columns contiguously
-// (lambda folded into mode 1) so every column load is coalesced, and clears
-// the spectrum accumulator.  (2) The fused sketch kernel: CTA (g, d) owns
+// (lambda folded into mode 1) so every column load is coalesced, clears
+// the spectrum accumulator and, for fcs_sketch_cp_seeded, writes the hash
+// tables of a seed (the same entries as fcs_make_hashes).  (2) The fused sketch kernel: CTA (g, d) owns
 // sketch d and a contiguous group of ranks and runs cp_run (P <= 8192) or
 // cp13_run (P = 16384) of fcs_cp_run.cuh: count sketch, block real FFT, mode
 // product and rank sum in the frequency domain (linearity moves the paper's
@@ -18,6 +19,7 @@
 #include <mutex>
 
 #include "fcs_cp_run.cuh"
+#include "fcs_hash.cuh"
 
 namespace fcs {
 namespace {
@@ -112,6 +114,11 @@ struct PrepArgs {
   float4 *zero;
   int64_t zero_n4;
   int zero_blocks;
+  // hash tables from a seed (hash_blocks = 0: none): D x hash_per_d blocks
+  HashArgs hs;
+  int32_t *h;
+  int8_t *s;
+  int64_t hash_per_d, hash_blocks;
 };
 
 __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a) {
@@ -145,8 +152,15 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a) {
     return;
   }
   const int64_t zb = b - a.ntile;
-  for (int64_t e = zb * 256 + tid; e < a.zero_n4; e += int64_t(a.zero_blocks) * 256)
-    a.zero[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (zb < a.zero_blocks) {
+    for (int64_t e = zb * 256 + tid; e < a.zero_n4; e += int64_t(a.zero_blocks) * 256)
+      a.zero[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const int64_t hb = zb - a.zero_blocks;           // < hash_blocks
+  const int d = int(hb / a.hash_per_d);
+  const int64_t e = (hb - d * a.hash_per_d) * 256 + tid;
+  if (e < a.hs.total) hash_entry(a.hs, d, e, a.h, a.s);
 }
 
 // Kernel for the given prefetch depth and scatter-buffer height.
@@ -230,11 +244,19 @@ int launch_cp(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
 
 using namespace fcs;
 
-extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
-                             const int32_t *host_J, int64_t R, int D,
-                             const float *const *host_U, const int64_t *host_ldU,
-                             const float *lambda, const int32_t *h, const int8_t *s,
-                             int64_t ldh, float *out) {
+namespace {
+
+// Hash tables to generate from a seed into (h, s) (fcs_sketch_cp_seeded).
+struct HashGen {
+  uint64_t seed;
+  int32_t *h;
+  int8_t *s;
+};
+
+int sketch_cp_impl(fcs_ctx *ctx, int N, const int64_t *host_I, const int32_t *host_J,
+                   int64_t R, int D, const float *const *host_U, const int64_t *host_ldU,
+                   const float *lambda, const int32_t *h, const int8_t *s, int64_t ldh,
+                   float *out, const HashGen *gen) {
   if (!ctx) return FCS_EINVAL;
   ctx->err.clear();
   CpArgs a{};
@@ -248,12 +270,18 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
     if (!host_U[n]) return set_error(ctx, FCS_EINVAL, "U[%d] is NULL", n);
     if (host_ldU[n] < R)
       return set_error(ctx, FCS_EINVAL, "ldU[%d]=%lld < R", n, (long long)host_ldU[n]);
+    if (gen && host_I[n] > (int64_t(1) << 32))
+      return set_error(ctx, FCS_EINVAL, "I[%d] too large for the hash family", n);
   }
   const int log2p = ilog2_ceil(a.m.Jt) < kMinLog2P ? kMinLog2P : ilog2_ceil(a.m.Jt);
   if (log2p > kMaxLog2PBig)
     return set_error(ctx, FCS_EUNSUPPORTED, "Jt=%lld needs FFT length > %d",
                      (long long)a.m.Jt, 1 << kMaxLog2PBig);
   if (log2p > kMaxLog2P) {
+    if (gen) {                          // long route: tables by their own launch
+      rc = fcs_make_hashes(ctx, gen->seed, N, host_I, host_J, D, gen->h, gen->s);
+      if (rc) return rc;
+    }
     DeviceGuard g(ctx->device);
     spec_cache_invalidate(ctx, out, sizeof(float) * size_t(D) * size_t(a.m.Jt));
     return big_sketch_cp(ctx, a.m, R, D, host_U, host_ldU, lambda, h, s, out, log2p);
@@ -294,8 +322,8 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
   DeviceGuard g(ctx->device);
   spec_cache_invalidate(ctx, out, sizeof(float) * size_t(D) * size_t(a.m.Jt));
   {
-    // one launch: factor transpose (lambda folded into mode 1) and clearing
-    // of the accumulator and tickets
+    // one launch: factor transpose (lambda folded into mode 1), clearing
+    // of the accumulator and tickets, and the hash tables of a seed
     PrepArgs pa{};
     for (int n = 0; n < N; ++n) {
       pa.t.U[n] = host_U[n];
@@ -312,7 +340,14 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
     pa.zero = static_cast<float4 *>(ws);
     pa.zero_n4 = int64_t(gbytes + cbytes) / 16;
     pa.zero_blocks = int(std::min<int64_t>(64, (pa.zero_n4 + 255) / 256));
-    const int64_t blocks = pa.ntile + pa.zero_blocks;
+    if (gen) {
+      pa.hs = hash_args(gen->seed, N, D, host_I, host_J);
+      pa.h = gen->h;
+      pa.s = gen->s;
+      pa.hash_per_d = (pa.hs.total + 255) / 256;
+      pa.hash_blocks = int64_t(D) * pa.hash_per_d;
+    }
+    const int64_t blocks = pa.ntile + pa.zero_blocks + pa.hash_blocks;
     if (blocks > 0x7fffffffLL) return set_error(ctx, FCS_EUNSUPPORTED, "factor matrices too large");
     prep_kernel<<<unsigned(blocks), 256, 0, ctx->stream>>>(pa);
     rc = check_cuda(ctx, cudaGetLastError(), "prep_kernel");
@@ -321,6 +356,26 @@ extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
   rc = FCS_EUNSUPPORTED;
   FCS_DISPATCH_LOG2M(log2m, rc = launch_cp<L>(ctx, a, groups, Imax));
   return rc;
+}
+
+}  // namespace
+
+extern "C" int fcs_sketch_cp(fcs_ctx *ctx, int N, const int64_t *host_I,
+                             const int32_t *host_J, int64_t R, int D,
+                             const float *const *host_U, const int64_t *host_ldU,
+                             const float *lambda, const int32_t *h, const int8_t *s,
+                             int64_t ldh, float *out) {
+  return sketch_cp_impl(ctx, N, host_I, host_J, R, D, host_U, host_ldU, lambda, h, s, ldh, out,
+                        nullptr);
+}
+
+extern "C" int fcs_sketch_cp_seeded(fcs_ctx *ctx, uint64_t seed, int N, const int64_t *host_I,
+                                    const int32_t *host_J, int64_t R, int D,
+                                    const float *const *host_U, const int64_t *host_ldU,
+                                    const float *lambda, int32_t *h, int8_t *s, float *out) {
+  const HashGen g{seed, h, s};
+  return sketch_cp_impl(ctx, N, host_I, host_J, R, D, host_U, host_ldU, lambda, h, s, 0, out,
+                        h && s ? &g : nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,9 +1,10 @@
 // fcs_host.cu -- fcs_sketch_cp_host: the CP-route sketch of eq. (FCS_syn)
 // from factor matrices in host memory to a sketch in host memory.  The call
 // copies the factors (and lambda) into a staging buffer the context owns,
-// generates the hash tables from the seed on the device (fcs_make_hashes),
-// runs fcs_sketch_cp and copies the D sketches back, all on the context's
-// stream; the host output is complete once that stream is synchronised.
+// generates the hash tables from the seed and sketches
+// (fcs_sketch_cp_seeded) and copies the D sketches back, all on the
+// context's stream; the host output is complete once that stream is
+// synchronised.
 // Host ranges that lie back to back in memory (factors stored one after
 // another, as in one staging block) move in one copy.
 #include <vector>
@@ -126,9 +127,8 @@ extern "C" int fcs_sketch_cp_host(fcs_ctx *ctx, int N, const int64_t *host_I,
     cudaError_t e = cudaMemcpyAsync(p.dst, p.src, p.bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return check_cuda(ctx, e, "cudaMemcpyAsync(H2D)");
   }
-  rc = fcs_make_hashes(ctx, seed, N, host_I, host_J, D, hd, sd);
-  if (rc) return rc;
-  rc = fcs_sketch_cp(ctx, N, host_I, host_J, R, D, Udev.data(), ld.data(), lamd, hd, sd, 0, od);
+  rc = fcs_sketch_cp_seeded(ctx, seed, N, host_I, host_J, R, D, Udev.data(), ld.data(), lamd, hd,
+                            sd, od);
   if (rc) return rc;
   return check_cuda(ctx, cudaMemcpyAsync(host_out, od, b_o, cudaMemcpyDeviceToHost, ctx->stream),
                     "cudaMemcpyAsync(D2H)");

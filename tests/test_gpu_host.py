@@ -1,7 +1,8 @@
-"""fcs_sketch_cp_host: the CP-route sketch from host factors to a host
-sketch (copies, hash generation, sketch and read-back queued by the library)
-must equal fcs_make_hashes + fcs_sketch_cp on device copies of the same
-inputs, and the oracle.  Needs a GPU."""
+"""fcs_sketch_cp_seeded (hash tables of a seed written by the factor
+transpose launch, then the sketch) and fcs_sketch_cp_host (the same from
+host factors to a host sketch: copies, tables, sketch and read-back queued by
+the library) must equal fcs_make_hashes + fcs_sketch_cp on device copies of
+the same inputs -- the tables bit for bit -- and the oracle.  Needs a GPU."""
 from __future__ import annotations
 
 import numpy as np
@@ -74,3 +75,54 @@ def test_host_pageable_strided_and_no_lambda(fcs, ctx):
         torch.cuda.synchronize()
         ref = _device_ref(fcs, ctx, U, None, J, D, seed)
         assert_sketch_close(out.numpy(), ref.astype(np.float64))
+
+
+@pytest.mark.parametrize("I,J,R,D", [
+    ([1000, 1000, 1000], [5000] * 3, 100, 10),        # the benchmark problem, P = 16384
+    ([100, 120, 90], [3000, 2000, 1000], 7, 3),       # P = 8192
+    ([300, 200, 250], [700, 900, 500], 12, 4),        # P = 4096
+    ([40, 50], [20, 30], 3, 2),                       # P = 64
+    ([7, 5, 6, 4, 3], [9, 8, 7, 6, 5], 2, 16),        # order 5, D = 16, P = 32
+    ([120, 100, 90], [9000, 8000, 7000], 6, 2),       # P = 32768: tables by their own launch
+])
+def test_seeded_equals_tables_then_sketch(fcs, ctx, orc, I, J, R, D):
+    U, lam = synth.cp_factors(81, I, R)
+    Ug, lg = [cuda(u) for u in U], cuda(lam)
+    out, h, s = fcs.fcs_sketch_cp_seeded(ctx, Ug, lg, J, D, seed=82)
+    h2, s2 = fcs.fcs_make_hashes(ctx, 82, I, J, D)
+    torch.cuda.synchronize()
+    assert torch.equal(h, h2) and torch.equal(s, s2)
+    ref = host(fcs.fcs_sketch_cp(ctx, Ug, lg, J, h2, s2))
+    assert_sketch_close(host(out), ref.astype(np.float64))
+    if sum(I) * D <= 20000:
+        ho, so = orc.make_hashes(82, I, J, D)
+        assert np.array_equal(host(h), ho) and np.array_equal(host(s), so)
+    if np.prod(I) * R <= 1e6:
+        ho, so = orc.make_hashes(82, I, J, D)
+        want = orc.fcs_cp([u.astype(np.float64) for u in U], lam.astype(np.float64), J, ho, so)
+        assert_sketch_close(host(out), want)
+
+
+def test_seeded_given_buffers_strided_no_lambda(fcs, ctx):
+    """Caller-given table and output buffers (reused by a second seed), a
+    factor that is a column slice of a wider matrix, no lambda; tables of the
+    wrong shape are refused before any launch."""
+    I, J, R, D = [300, 200, 250], [5000, 4000, 3000], 12, 5          # P = 16384
+    U, _ = synth.cp_factors(83, I, R)
+    Ug = [cuda(u) for u in U]
+    Ug[1] = cuda(synth.gaussian(84, (I[1], R + 5)))[:, 2:2 + R]   # a column slice on the device
+    assert Ug[1].stride(0) == R + 5
+    tot = sum(I)
+    h = torch.empty((D, tot), dtype=torch.int32, device="cuda")
+    s = torch.empty((D, tot), dtype=torch.int8, device="cuda")
+    out = torch.empty((D, sum(J) - 2), dtype=torch.float32, device="cuda")
+    for seed in (85, 86):
+        o, hh, ss = fcs.fcs_sketch_cp_seeded(ctx, Ug, None, J, D, seed, out=out, h=h, s=s)
+        assert o.data_ptr() == out.data_ptr() and hh.data_ptr() == h.data_ptr()
+        h2, s2 = fcs.fcs_make_hashes(ctx, seed, I, J, D)
+        ref = host(fcs.fcs_sketch_cp(ctx, Ug, None, J, h2, s2))
+        torch.cuda.synchronize()
+        assert torch.equal(h, h2) and torch.equal(s, s2)
+        assert_sketch_close(host(out), ref.astype(np.float64))
+    with pytest.raises(ValueError):
+        fcs.fcs_sketch_cp_seeded(ctx, Ug, None, J, D, 87, h=h[:, :tot - 1].contiguous(), s=s)
