@@ -80,6 +80,12 @@ int fcs_version(void);
  * (a cudaStream_t; NULL = the legacy default stream).  `mem_budget_bytes`
  * caps the workspace the context may hold; (size_t)-1 means no cap, 0 means
  * no workspace at all (calls that need one return FCS_ENOMEM_BUDGET).
+ * The workspace and the other context buffers grow on demand, ordered on the
+ * context's stream (stream-ordered allocation: the old buffer is released
+ * once the work queued before has run), so growth neither waits on the host
+ * nor synchronises the device.  A call that would grow a buffer while the
+ * stream is being captured into a CUDA graph returns FCS_EINVAL: make the
+ * same call once before capturing.
  * Allocates the twiddle table (exp(-2 pi i k / 32768), k < 32768, computed in
  * FP64 on the device and rounded to FP32).  *ctx is NULL on failure. */
 int fcs_create(fcs_ctx **ctx, int device, void *stream, size_t mem_budget_bytes);

@@ -30,25 +30,7 @@ constexpr int kMaxRank = 32;
 // Scratch for the decompositions, separate from the workspace that the
 // calls below use.
 int ensure_algo(fcs_ctx *ctx, size_t bytes) {
-  bytes = (bytes + 255) & ~size_t(255);
-  if (bytes <= ctx->algo_bytes) return FCS_OK;
-  if (bytes > ctx->budget)
-    return set_error(ctx, FCS_ENOMEM_BUDGET, "scratch of %zu bytes exceeds the budget", bytes);
-  if (ctx->algo) {
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaStreamSynchronize");
-    cudaFree(ctx->algo);
-    ctx->algo = nullptr;
-    ctx->algo_bytes = 0;
-  }
-  cudaError_t e = cudaMalloc(&ctx->algo, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    ctx->algo = nullptr;
-    return check_cuda(ctx, e, "cudaMalloc(decomposition scratch)");
-  }
-  ctx->algo_bytes = bytes;
-  return FCS_OK;
+  return grow_buffer(ctx, &ctx->algo, &ctx->algo_bytes, bytes, "decomposition scratch");
 }
 
 __device__ __forceinline__ float block_sum(float v, float *red) {

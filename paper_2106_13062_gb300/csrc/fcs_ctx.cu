@@ -23,57 +23,50 @@ int check_cuda(fcs_ctx *ctx, cudaError_t e, const char *what) {
   return set_error(ctx, FCS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-int ensure_workspace(fcs_ctx *ctx, size_t bytes, void **out) {
+int grow_buffer(fcs_ctx *ctx, void **buf, size_t *have, size_t bytes, const char *what) {
   bytes = (bytes + 255) & ~size_t(255);
-  if (bytes <= ctx->ws_bytes) {
-    *out = ctx->ws;
-    return FCS_OK;
+  if (bytes <= *have) return FCS_OK;
+  if (bytes > ctx->budget)
+    return set_error(ctx, FCS_ENOMEM_BUDGET, "%s of %zu bytes exceeds the context budget of %zu",
+                     what, bytes, ctx->budget);
+  DeviceGuard g(ctx->device);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(ctx->stream, &cs);
+  if (e != cudaSuccess) return check_cuda(ctx, e, "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone)
+    return set_error(ctx, FCS_EINVAL,
+                     "%s would grow to %zu bytes while the stream is being captured: make the "
+                     "same call once before capturing",
+                     what, bytes);
+  if (*buf) {
+    // released after the work already queued on the stream has run
+    e = cudaFreeAsync(*buf, ctx->stream);
+    *buf = nullptr;
+    *have = 0;
+    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFreeAsync");
   }
-  if (bytes > ctx->budget) {
-    return set_error(ctx, FCS_ENOMEM_BUDGET,
-                     "workspace of %zu bytes exceeds the context budget of %zu",
-                     bytes, ctx->budget);
-  }
-  if (ctx->ws) {
-    // the old buffer may still be in use by queued work
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaStreamSynchronize");
-    cudaFree(ctx->ws);
-    ctx->ws = nullptr;
-    ctx->ws_bytes = 0;
-  }
-  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  e = cudaMallocAsync(buf, bytes, ctx->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    ctx->ws = nullptr;
-    return check_cuda(ctx, e, "cudaMalloc(workspace)");
+    *buf = nullptr;
+    return check_cuda(ctx, e, "cudaMallocAsync");
   }
-  ctx->ws_bytes = bytes;
+  *have = bytes;
+  return FCS_OK;
+}
+
+int ensure_workspace(fcs_ctx *ctx, size_t bytes, void **out) {
+  int rc = grow_buffer(ctx, &ctx->ws, &ctx->ws_bytes, bytes, "workspace");
+  if (rc) return rc;
   *out = ctx->ws;
   return FCS_OK;
 }
 
 int ensure_raw(fcs_ctx *ctx, size_t bytes) {
-  bytes = (bytes + 255) & ~size_t(255);
-  if (bytes <= ctx->raw_bytes) return FCS_OK;
-  if (bytes > ctx->budget)
-    return set_error(ctx, FCS_ENOMEM_BUDGET, "buffer of %zu bytes exceeds the context budget",
-                     bytes);
-  if (ctx->raw) {
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaStreamSynchronize");
-    cudaFree(ctx->raw);
-    ctx->raw = nullptr;
-    ctx->raw_bytes = 0;
-  }
-  cudaError_t e = cudaMalloc(&ctx->raw, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    ctx->raw = nullptr;
-    return check_cuda(ctx, e, "cudaMalloc(raw)");
-  }
-  ctx->raw_bytes = bytes;
-  return FCS_OK;
+  void *p = ctx->raw;
+  const int rc = grow_buffer(ctx, &p, &ctx->raw_bytes, bytes, "buffer");
+  ctx->raw = static_cast<float *>(p);
+  return rc;
 }
 
 namespace {
@@ -185,7 +178,11 @@ extern "C" int fcs_create(fcs_ctx **out, int device, void *stream, size_t budget
 extern "C" int fcs_destroy(fcs_ctx *ctx) {
   if (!ctx) return FCS_OK;
   DeviceGuard g(ctx->device);
-  cudaStreamSynchronize(ctx->stream);
+  // the buffers are stream-ordered allocations: nothing may still use them
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    cudaDeviceSynchronize();
+  }
   batch_state_destroy(ctx);
   spec_cache_destroy(ctx);
   if (ctx->ws) cudaFree(ctx->ws);

@@ -15,29 +15,10 @@ namespace fcs {
 namespace {
 
 // Grow the context's host-copy staging buffer to `bytes` (previous contents
-// are not kept; queued work that may still read it is waited for first).
+// are not kept; stream-ordered, as every context buffer).
 int ensure_stage(fcs_ctx *ctx, size_t bytes, void **out) {
-  bytes = (bytes + 255) & ~size_t(255);
-  if (bytes > ctx->stage_bytes) {
-    if (bytes > ctx->budget)
-      return set_error(ctx, FCS_ENOMEM_BUDGET,
-                       "staging buffer of %zu bytes exceeds the context budget of %zu", bytes,
-                       ctx->budget);
-    if (ctx->stage) {
-      cudaError_t e = cudaStreamSynchronize(ctx->stream);
-      if (e != cudaSuccess) return check_cuda(ctx, e, "cudaStreamSynchronize");
-      cudaFree(ctx->stage);
-      ctx->stage = nullptr;
-      ctx->stage_bytes = 0;
-    }
-    cudaError_t e = cudaMalloc(&ctx->stage, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      ctx->stage = nullptr;
-      return check_cuda(ctx, e, "cudaMalloc(staging)");
-    }
-    ctx->stage_bytes = bytes;
-  }
+  int rc = grow_buffer(ctx, &ctx->stage, &ctx->stage_bytes, bytes, "staging buffer");
+  if (rc) return rc;
   *out = ctx->stage;
   return FCS_OK;
 }

@@ -61,6 +61,13 @@ void batch_state_destroy(fcs_ctx *ctx);
 void spec_cache_invalidate(fcs_ctx *ctx, const void *p, size_t bytes);
 void spec_cache_destroy(fcs_ctx *ctx);
 int check_cuda(fcs_ctx *ctx, cudaError_t e, const char *what);
+// Grow a context-owned device buffer (*buf, *have bytes) to at least `bytes`
+// (rounded up to 256; contents are not kept), ordered on the context's
+// stream: the old buffer is released once the work queued before the call
+// has run, and the new one is ready for the work queued after it, with no
+// host wait and no device synchronisation.  Refused (FCS_EINVAL) while the
+// stream is being captured: make the same call once before capturing.
+int grow_buffer(fcs_ctx *ctx, void **buf, size_t *have, size_t bytes, const char *what);
 // Grow the workspace to at least `bytes` (contents are not preserved).
 int ensure_workspace(fcs_ctx *ctx, size_t bytes, void **out);
 // Grow ctx->raw to at least `bytes` (counted against the budget with the workspace).

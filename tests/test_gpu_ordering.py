@@ -4,8 +4,8 @@ workspace, calls of different shapes one after another on a fresh
 context, a sketch right after a batch chain (whose kernels release their
 dependents early), inputs copied on another stream, CUDA-graph capture and
 replay with the inputs changed in place between replays, and a graph that
-reads every output of a batch plan right after the plan's launch.  Needs a
-GPU."""
+reads every output of a batch plan right after the plan's launch, and
+workspace growth while earlier calls are still queued.  Needs a GPU."""
 from __future__ import annotations
 
 import numpy as np
@@ -207,4 +207,32 @@ def test_persistent_accumulator_across_sketch_counts(fcs, orc):
         refs.append(_ref(orc, U, lam, Js, 700 + k, D))
     for k in range(len(outs)):
         assert_sketch_close(host(outs[k]), refs[k], what=f"call {k}")
+    c.close()
+
+
+def test_workspace_grows_while_earlier_calls_are_queued(fcs, orc):
+    """Calls of growing size queued back to back on a fresh context with no
+    host synchronisation in between: every growth of the context's
+    workspace is ordered on the stream (the old buffer is released only
+    after the calls queued before have run), so each call still reads its
+    own buffer.  Short, P = 16384, P = 32768 and two-pass (P = 2^17) routes;
+    all results against the oracle at the end."""
+    c = fcs.Context()
+    seq = [([20, 30], [10, 12], 3, 1),                          # P = 32
+           ([300, 200], [2000, 1500], 12, 9),                   # P = 4096
+           ([700, 600, 800], [5000, 4000, 6000], 30, 16),       # P = 16384
+           ([120, 100, 90], [9000, 8000, 7000], 6, 2),          # P = 32768
+           ([60, 50, 40], [40000, 30000, 20000], 3, 2)]         # P = 2^17, two-pass route
+    inputs = []
+    for k, (Is, Js, R, D) in enumerate(seq):
+        U, lam = synth.cp_factors(450 + k, Is, R)
+        inputs.append((U, lam, [cuda(u) for u in U], cuda(lam)))
+    torch.cuda.synchronize()
+    outs = []
+    for k, ((Is, Js, R, D), (_, _, Ug, lg)) in enumerate(zip(seq, inputs)):
+        out, _, _ = fcs.fcs_sketch_cp_seeded(c, Ug, lg, Js, D, 550 + k)
+        outs.append(out)
+    torch.cuda.synchronize()
+    for k, ((Is, Js, R, D), (U, lam, _, _)) in enumerate(zip(seq, inputs)):
+        assert_sketch_close(host(outs[k]), _ref(orc, U, lam, Js, 550 + k, D), what=f"call {k}")
     c.close()
