@@ -6,7 +6,9 @@
 // Two kernels.  (1) prep_kernel writes the factor columns contiguously
 // (lambda folded into mode 1) so every column load is coalesced, clears
 // the spectrum accumulator and, for fcs_sketch_cp_seeded, writes the hash
-// tables of a seed (the same entries as fcs_make_hashes).  (2) The fused sketch kernel: CTA (g, d) owns
+// tables of a seed (the same entries as fcs_make_hashes).  The sketch kernel
+// is its programmatic dependent: placed while prep runs, it waits for the
+// prep grid at its first instruction.  (2) The fused sketch kernel: CTA (g, d) owns
 // sketch d and a contiguous group of ranks and runs cp_run (P <= 8192) or
 // cp13_run (P = 16384) of fcs_cp_run.cuh: count sketch, block real FFT, mode
 // product and rank sum in the frequency domain (linearity moves the paper's
@@ -69,9 +71,19 @@ struct CpView {
   __device__ __forceinline__ unsigned *ticket(int d) const { return a.counter + d; }
 };
 
+// The sketch kernels of fcs_sketch_cp are launched as programmatic dependents
+// of the prep launch, so their CTAs are placed while prep runs.  Every one of
+// them waits for the prep grid to complete (and its writes to be visible:
+// transposed factors, cleared accumulator and tickets, hash tables) before
+// anything else; launched the ordinary way the wait returns at once.
+__device__ __forceinline__ void wait_for_prep() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // CTA (g, d): ranks [g * ranks_per_cta, ...) of sketch d.
 template <int LOG2M, int NT, int CPT>
 __global__ void __launch_bounds__(NT) cp_kernel(CpArgs a, const float2 *__restrict__ tw) {
+  wait_for_prep();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int is_last;
   const int64_t r0 = blockIdx.x * a.ranks_per_cta;
@@ -84,6 +96,7 @@ __global__ void __launch_bounds__(NT) cp_kernel(CpArgs a, const float2 *__restri
 // blocks per scatter-buffer row (ra <= 32 RMAX).
 template <int CPT, int RMAX>
 __global__ void __launch_bounds__(wdit::kNT) cp13_kernel(CpArgs a, const float2 *__restrict__ tw) {
+  wait_for_prep();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int is_last;
   const int64_t r0 = blockIdx.x * a.ranks_per_cta;
@@ -97,6 +110,7 @@ __global__ void __launch_bounds__(wdit::kNT) cp13_kernel(CpArgs a, const float2 
 template <int CPT, int RMAX>
 __global__ void __launch_bounds__(wdit::w12::kNT, 2) cp12_kernel(CpArgs a,
                                                                  const float2 *__restrict__ tw) {
+  wait_for_prep();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int is_last;
   const int64_t r0 = blockIdx.x * a.ranks_per_cta;
@@ -122,6 +136,8 @@ struct PrepArgs {
 };
 
 __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a) {
+  // the sketch kernel may be placed now; it waits for this grid to complete
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int64_t b = blockIdx.x;
   const int tid = threadIdx.x;
   if (b < a.ntile) {
@@ -178,6 +194,23 @@ const void *cp13_pick(int64_t Imax, int sb) {
   return cp13_pick_rmax<4>(ra);
 }
 
+// Launch a sketch kernel as a programmatic dependent of the prep launch
+// before it on the context's stream.
+cudaError_t launch_after_prep(fcs_ctx *ctx, const void *kern, dim3 grid, dim3 block, size_t smem,
+                              void **args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, kern, args);
+}
+
 int launch_cp13(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
   const size_t smem = Cp13Smem::bytes((a.sb + 31) >> 5);
   const void *kern = cp13_pick(Imax, a.sb);
@@ -186,8 +219,8 @@ int launch_cp13(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
   if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp13)");
   const float2 *twp = ctx->twiddle;
   void *args[] = {&a, &twp};
-  e = cudaLaunchKernel(kern, dim3(unsigned(groups), unsigned(a.D)), dim3(wdit::kNT), args, smem,
-                       ctx->stream);
+  e = launch_after_prep(ctx, kern, dim3(unsigned(groups), unsigned(a.D)), dim3(wdit::kNT), smem,
+                        args);
   return check_cuda(ctx, e, "cp13_kernel");
 }
 
@@ -209,8 +242,8 @@ int launch_cp12(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
   if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp12)");
   const float2 *twp = ctx->twiddle;
   void *args[] = {&a, &twp};
-  e = cudaLaunchKernel(kern, dim3(unsigned(groups), unsigned(a.D)), dim3(wdit::w12::kNT), args,
-                       smem, ctx->stream);
+  e = launch_after_prep(ctx, kern, dim3(unsigned(groups), unsigned(a.D)), dim3(wdit::w12::kNT),
+                        smem, args);
   return check_cuda(ctx, e, "cp12_kernel");
 }
 
@@ -230,8 +263,13 @@ int launch_cp(fcs_ctx *ctx, CpArgs &a, int64_t groups, int64_t Imax) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return check_cuda(ctx, e, "cudaFuncSetAttribute(cp)");
       }
-      kern<<<dim3(unsigned(groups), unsigned(a.D)), NT, smem, ctx->stream>>>(a, ctx->twiddle);
-      return check_cuda(ctx, cudaGetLastError(), "cp_kernel");
+      const float2 *twp = ctx->twiddle;
+      void *args[] = {&a, &twp};
+      return check_cuda(ctx,
+                        launch_after_prep(ctx, reinterpret_cast<const void *>(kern),
+                                          dim3(unsigned(groups), unsigned(a.D)), dim3(NT), smem,
+                                          args),
+                        "cp_kernel");
     };
     if (cpt <= 1) return go(cp_kernel<LOG2M, NT, 1>);
     if (cpt <= 2) return go(cp_kernel<LOG2M, NT, 2>);
