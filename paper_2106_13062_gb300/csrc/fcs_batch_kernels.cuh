@@ -30,6 +30,11 @@ struct BatchProb {
 struct BatchView {
   const BatchProb &P;
   int sb;
+  // factor columns and tables, written before the chain's first class
+  template <class T>
+  __device__ __forceinline__ T ld(const T *p) const {
+    return __ldg(p);
+  }
   __device__ __forceinline__ int modes() const { return P.N; }
   __device__ __forceinline__ int64_t dim(int n) const { return P.I[n]; }
   __device__ __forceinline__ const float *column(int n, int64_t r) const {

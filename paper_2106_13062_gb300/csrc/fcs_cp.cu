@@ -54,6 +54,14 @@ struct TransposeArgs {
 struct CpView {
   const CpArgs &a;
   int sb;
+  // inputs written by the prep launch, which may still run when the sketch
+  // kernel (its programmatic dependent) starts: ordinary cached loads (after
+  // the grid wait), not the read-only path, whose data must not change
+  // during the kernel
+  template <class T>
+  __device__ __forceinline__ T ld(const T *p) const {
+    return __ldca(p);
+  }
   __device__ __forceinline__ int modes() const { return a.m.N; }
   __device__ __forceinline__ int64_t dim(int n) const { return a.m.I[n]; }
   __device__ __forceinline__ const float *column(int n, int64_t r) const {

@@ -86,9 +86,9 @@ __device__ __forceinline__ void cp_run(const Prob &a, int d, int64_t r0, int64_t
       ph[c] = -1;
       pv[c] = 0.f;
       if (i < In) {
-        const float v = __ldg(col + i);
-        pv[c] = __ldg(sn + i) < 0 ? -v : v;
-        ph[c] = __ldg(hn + i);
+        const float v = a.ld(col + i);
+        pv[c] = a.ld(sn + i) < 0 ? -v : v;
+        ph[c] = a.ld(hn + i);
       }
     }
   };
@@ -108,9 +108,9 @@ __device__ __forceinline__ void cp_run(const Prob &a, int d, int64_t r0, int64_t
         const int32_t *hn = a.hashes(d, n);
         const int8_t *sn = a.signs(d, n);
         for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
-          const int hb = __ldg(hn + i);
-          const float v = __ldg(col + i);
-          if (unsigned(hb) < unsigned(sb)) atomicAdd(A + hb, __ldg(sn + i) < 0 ? -v : v);
+          const int hb = a.ld(hn + i);
+          const float v = a.ld(col + i);
+          if (unsigned(hb) < unsigned(sb)) atomicAdd(A + hb, a.ld(sn + i) < 0 ? -v : v);
         }
       }
       // prefetch the next column while this one is transformed
@@ -248,9 +248,9 @@ __device__ __forceinline__ void cp13_run(const Prob &a, int d, int64_t r0, int64
       ph[c] = -1;
       pv[c] = 0.f;
       if (i < In) {
-        const float v = __ldg(col + i);
-        pv[c] = __ldg(sn + i) < 0 ? -v : v;
-        ph[c] = __ldg(hn + i);
+        const float v = a.ld(col + i);
+        pv[c] = a.ld(sn + i) < 0 ? -v : v;
+        ph[c] = a.ld(hn + i);
       }
     }
   };
@@ -265,10 +265,10 @@ __device__ __forceinline__ void cp13_run(const Prob &a, int d, int64_t r0, int64
       const int32_t *hn = a.hashes(d, n);
       const int8_t *sn = a.signs(d, n);
       for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
-        const int hb = __ldg(hn + i);
-        const float v = __ldg(col + i);
+        const int hb = a.ld(hn + i);
+        const float v = a.ld(col + i);
         if (unsigned(hb) < unsigned(sb))
-          atomicAdd(A + wdit::a_index(hb, ra), __ldg(sn + i) < 0 ? -v : v);
+          atomicAdd(A + wdit::a_index(hb, ra), a.ld(sn + i) < 0 ? -v : v);
       }
     }
   };
@@ -452,9 +452,9 @@ __device__ __forceinline__ void cp12_run(const Prob &a, int d, int64_t r0, int64
       ph[c] = -1;
       pv[c] = 0.f;
       if (i < In) {
-        const float v = __ldg(col + i);
-        pv[c] = __ldg(sn + i) < 0 ? -v : v;
-        ph[c] = __ldg(hn + i);
+        const float v = a.ld(col + i);
+        pv[c] = a.ld(sn + i) < 0 ? -v : v;
+        ph[c] = a.ld(hn + i);
       }
     }
   };
@@ -468,10 +468,10 @@ __device__ __forceinline__ void cp12_run(const Prob &a, int d, int64_t r0, int64
       const int32_t *hn = a.hashes(d, n);
       const int8_t *sn = a.signs(d, n);
       for (int64_t i = int64_t(CPT) * NT + tid; i < In; i += NT) {
-        const int hb = __ldg(hn + i);
-        const float v = __ldg(col + i);
+        const int hb = a.ld(hn + i);
+        const float v = a.ld(col + i);
         if (unsigned(hb) < unsigned(sb))
-          atomicAdd(A + W::a_index(hb, ra), __ldg(sn + i) < 0 ? -v : v);
+          atomicAdd(A + W::a_index(hb, ra), a.ld(sn + i) < 0 ? -v : v);
       }
     }
   };

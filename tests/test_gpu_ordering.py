@@ -152,6 +152,45 @@ def test_graph_capture_and_replay(fcs, ctx, orc):
     torch.cuda.current_stream().wait_stream(st)
 
 
+@pytest.mark.parametrize("Is,Js,R,D", [
+    (I, J, 30, 4),                                       # P = 16384
+    ([500, 400, 600], [3000, 2500, 2000], 20, 5),        # P = 8192
+    (I2, J2, 12, 6),                                     # P = 4096
+])
+def test_graph_replays_of_the_seeded_call(fcs, orc, Is, Js, R, D):
+    """fcs_sketch_cp_seeded (prep launch, then the sketch kernel as its
+    programmatic dependent) captured once and replayed four times, the factors
+    changed in place before each replay: every replay must equal a direct call
+    on the new values (and the first one the oracle), so the sketch kernel
+    never reads what prep has not yet written."""
+    c = fcs.Context()
+    U, lam = synth.cp_factors(260, Is, R)
+    Ug = [cuda(u) for u in U]
+    lamg = cuda(lam)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        out, h, s = fcs.fcs_sketch_cp_seeded(c, Ug, lamg, Js, D, 360)   # buffers sized
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=st):
+            fcs.fcs_sketch_cp_seeded(c, Ug, lamg, Js, D, 361, out=out, h=h, s=s)
+    torch.cuda.current_stream().wait_stream(st)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    for k in range(4):
+        for u in Ug:
+            u.mul_(-1.3).add_(torch.randn(u.shape, device="cuda", generator=gen))
+        g.replay()
+        torch.cuda.synchronize()
+        got = host(out).copy()
+        if k == 0:
+            Uh = [host(u).astype(np.float64) for u in Ug]
+            assert_sketch_close(got, _ref(orc, Uh, lam, Js, 361, D), what="replay 0 vs oracle")
+        ref, _, _ = fcs.fcs_sketch_cp_seeded(c, Ug, lamg, Js, D, 361)
+        assert_sketch_close(got, host(ref).astype(np.float64), what=f"replay {k}")
+    c.close()
+
+
 def test_graph_reads_batch_outputs_after_the_chain(fcs, ctx, orc):
     """A graph that launches a batch plan (one class kernel per FFT size,
     chained) and then copies every output: the copies must see every class
