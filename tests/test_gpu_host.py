@@ -84,6 +84,9 @@ def test_host_pageable_strided_and_no_lambda(fcs, ctx):
     ([40, 50], [20, 30], 3, 2),                       # P = 64
     ([7, 5, 6, 4, 3], [9, 8, 7, 6, 5], 2, 16),        # order 5, D = 16, P = 32
     ([120, 100, 90], [9000, 8000, 7000], 6, 2),       # P = 32768: tables by their own launch
+    ([3000], [6000], 4, 1),                           # one mode, one sketch, P = 8192
+    ([6, 5, 4, 3, 4, 5, 6, 3], [7, 6, 5, 4, 5, 6, 7, 4], 2, 3),   # order 8, P = 64
+    ([300, 200, 250], [100000, 90000, 80000], 2, 2),  # P = 2^18: two-pass route (no oracle sketch)
 ])
 def test_seeded_equals_tables_then_sketch(fcs, ctx, orc, I, J, R, D):
     U, lam = synth.cp_factors(81, I, R)
