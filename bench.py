@@ -481,11 +481,47 @@ class KronWorkload:
                 self.rh.numel() * 4)
 
     def e2e_step(self, k):
-        self.Ad.copy_(self.Ah, non_blocking=True)
-        self.Bd.copy_(self.Bh, non_blocking=True)
-        self.idd.copy_(self.ih, non_blocking=True)
-        rec = self.step(k, lambda _: None, A=self.Ad, B=self.Bd, idx=self.idd)
-        self.rh.copy_(rec, non_blocking=True)
+        """Pipelined over chunks of pairs on three streams: the upload of
+        chunk c + 1 runs while chunk c is sketched, combined and recovered and
+        chunk c - 1 is read back (the link is the bound: its two directions
+        overlap, and the compute hides under the upload)."""
+        import torch
+        fcs, n = self.fcs, self.n
+        main = torch.cuda.current_stream(self.dev)
+        if not hasattr(self, "st_in"):
+            self.st_in, self.st_cmp, self.st_out = (torch.cuda.Stream(self.dev) for _ in range(3))
+        st_in, st_cmp, st_out = self.st_in, self.st_cmp, self.st_out
+        for st in (st_in, st_cmp, st_out):
+            st.wait_stream(main)
+        chunks = 8
+        per = self.pairs // chunks
+        with torch.cuda.stream(st_cmp):
+            h, s = fcs.fcs_make_hashes(self.ctx, self.seed + k, self.I4, self.J4, self.D)
+        for c in range(chunks):
+            lo, hi = c * per, (c + 1) * per
+            with torch.cuda.stream(st_in):
+                self.Ad[lo:hi].copy_(self.Ah[lo:hi], non_blocking=True)
+                self.Bd[lo:hi].copy_(self.Bh[lo:hi], non_blocking=True)
+                self.idd[lo:hi].copy_(self.ih[lo:hi], non_blocking=True)
+                ev_in = torch.cuda.Event()
+                ev_in.record(st_in)
+            with torch.cuda.stream(st_cmp):
+                st_cmp.wait_event(ev_in)
+                fcs.fcs_sketch_dense(self.ctx, self.Ad[lo:hi], self.J4[:2], h[:, :2 * n],
+                                     s[:, :2 * n], ldh=4 * n, batched=True, out=self.fa[lo:hi])
+                fcs.fcs_sketch_dense(self.ctx, self.Bd[lo:hi], self.J4[2:], h[:, 2 * n:],
+                                     s[:, 2 * n:], ldh=4 * n, batched=True, out=self.fb[lo:hi])
+                sk = fcs.fcs_sketch_outer(self.ctx, self.fa[lo:hi], self.fb[lo:hi])
+                rec = fcs.fcs_recover(self.ctx, sk, self.I4, self.J4, h, s, self.idd[lo:hi])
+                ev_out = torch.cuda.Event()
+                ev_out.record(st_cmp)
+            with torch.cuda.stream(st_out):
+                st_out.wait_event(ev_out)
+                self.rh[lo:hi].copy_(rec, non_blocking=True)
+                rec.record_stream(st_out)
+                sk.record_stream(st_out)
+        for st in (st_in, st_cmp, st_out):
+            main.wait_stream(st)
 
     def check(self):
         import torch
