@@ -448,6 +448,17 @@ class KronWorkload:
         self.fa = torch.empty((self.pairs, self.D, self.Ja), dtype=torch.float32, device=dev)
         self.fb = torch.empty_like(self.fa)
         self.fcs, self.ctx, self.dev = fcs, ctx, dev
+        # the outer combine's block shape, tuned for this batch and for the
+        # end-to-end leg's chunks (untimed)
+        h, s = fcs.fcs_make_hashes(ctx, self.seed, self.I4, self.J4, self.D)
+        ld, n = 4 * self.n, self.n
+        fcs.fcs_sketch_dense(ctx, self.Ag, self.J4[:2], h[:, :2 * n], s[:, :2 * n], ldh=ld,
+                             batched=True, out=self.fa)
+        fcs.fcs_sketch_dense(ctx, self.Bg, self.J4[2:], h[:, 2 * n:], s[:, 2 * n:], ldh=ld,
+                             batched=True, out=self.fb)
+        self.outer_threads, _ = fcs.fcs_outer_autotune(ctx, self.fa, self.fb)
+        per = self.pairs // 8
+        fcs.fcs_outer_autotune(ctx, self.fa[:per], self.fb[:per])
 
     def step(self, k, marks, A=None, B=None, idx=None):
         fcs = self.fcs
@@ -544,6 +555,7 @@ class KronWorkload:
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)",
                 "bytes_per_launch": by, "avg_launch_ms": t,
                 "dense_ms": td, "outer_ms": statistics.mean(times_ms["outer"]),
+                "outer_threads": self.outer_threads,
                 "recover_ms": tr}
 
     def oracle_sample(self, budget_s=12.0):

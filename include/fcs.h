@@ -582,6 +582,24 @@ int fcs_sketch_outer(fcs_ctx *ctx, int64_t nbatch, int D, int64_t La,
 int fcs_sketch_outer_sum(fcs_ctx *ctx, int64_t nbatch, int64_t L, int D, int64_t La, int64_t Lb,
                          const float *fa, const float *fb, float *out);
 
+/*
+ * fcs_outer_autotune -- choose the block shape of fcs_sketch_outer /
+ * fcs_sketch_outer_sum for one problem shape (nbatch, L, D, La, Lb; L = 1 for
+ * fcs_sketch_outer).  Each (item, sketch) runs on one CTA whose real FFTs use
+ * M/16 threads (M = P/2, at least a warp) or twice that; the call runs both
+ * on the given buffers (writing `out` several times, synchronising the
+ * context's stream) and keeps the twice-as-many-threads shape for this
+ * device and shape only when it is at least 3 % faster.  Later calls of the
+ * same shape, in any context on this device, use the choice.  Shapes with
+ * P > 16384 (the two-pass route) have one shape.  *host_threads (may be
+ * NULL) receives the chosen block size (0 for P > 16384).  When the call
+ * returns, `out` holds the result of the shape run last (the
+ * twice-as-many-threads one where there are two); it is complete once the
+ * context's stream has been synchronised.
+ */
+int fcs_outer_autotune(fcs_ctx *ctx, int64_t nbatch, int64_t L, int D, int64_t La, int64_t Lb,
+                       const float *fa, const float *fb, float *out, int *host_threads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,9 @@ def lib() -> C.CDLL:
                                                C.c_int64, vp, vp, vp, vp]),
                 "fcs_sketch_outer_sum": (C.c_int, [vp, C.c_int64, C.c_int64, C.c_int,
                                                    C.c_int64, C.c_int64, vp, vp, vp]),
+                "fcs_outer_autotune": (C.c_int, [vp, C.c_int64, C.c_int64, C.c_int,
+                                                 C.c_int64, C.c_int64, vp, vp, vp,
+                                                 C.POINTER(C.c_int)]),
                 "fcs_rtpm": (C.c_int, [vp, C.c_int, C.c_int64, i32p, C.c_int, vp, vp,
                                        vp, C.c_int64, C.c_int, C.c_int, C.c_int, vp,
                                        vp, vp]),
@@ -210,7 +213,7 @@ def exported_symbols():
             "fcs_sketch_cp_host",
             "fcs_contract", "fcs_contract_both", "fcs_cache_spectra", "fcs_forget",
             "fcs_fold", "fcs_sketch_inner", "fcs_rtpm", "fcs_als",
-            "fcs_recover", "fcs_sketch_outer", "fcs_sketch_outer_sum",
+            "fcs_recover", "fcs_sketch_outer", "fcs_sketch_outer_sum", "fcs_outer_autotune",
             "fcs_batch_plan_create", "fcs_batch_plan_launch",
             "fcs_batch_plan_destroy", "fcs_batch_sketch_cp", "fcs_batch_autotune",
             "fcs_batch_plan_create_cfg", "fcs_batch_plan_config",
@@ -692,6 +695,29 @@ def fcs_sketch_outer_sum(ctx: Context, fa: torch.Tensor, fb: torch.Tensor):
     ctx.check(lib().fcs_sketch_outer_sum(ctx.handle, nb, Ls, D, La, Lb, _ptr(fa),
                                          _ptr(fb), _ptr(out)))
     return out
+
+
+def fcs_outer_autotune(ctx: Context, fa: torch.Tensor, fb: torch.Tensor, slices: bool = False) -> int:
+    """Choose the block size of fcs_sketch_outer (slices=False: fa [.., D, La])
+    or fcs_sketch_outer_sum (slices=True: fa [.., L, D, La]) for this shape by
+    timing both on these inputs; later calls of the shape use it.  Returns
+    (block size chosen, 0 for the two-pass route; the output of the shape
+    timed last)."""
+    ctx._sync_stream()
+    _need(fa, torch.float32, "fa")
+    _need(fb, torch.float32, "fb")
+    if fa.shape[:-1] != fb.shape[:-1] or (slices and fa.dim() < 3):
+        raise ValueError("fa and fb must share leading dimensions")
+    Ls = fa.shape[-3] if slices else 1
+    D = fa.shape[-2]
+    La, Lb = fa.shape[-1], fb.shape[-1]
+    nb = fa.numel() // (Ls * D * La)
+    lead = fa.shape[:-3] if slices else fa.shape[:-2]
+    out = torch.empty(tuple(lead) + (D, La + Lb - 1), dtype=torch.float32, device=fa.device)
+    nt = C.c_int(0)
+    ctx.check(lib().fcs_outer_autotune(ctx.handle, nb, Ls, D, La, Lb, _ptr(fa), _ptr(fb),
+                                       _ptr(out), C.byref(nt)))
+    return nt.value, out
 
 
 def fcs_fold(ctx: Context, x: torch.Tensor, J: int):

@@ -385,6 +385,32 @@ def test_outer_combine(fcs, ctx, orc, nb, D, La, Lb):
         assert_sketch_close(got[b], ref)
 
 
+@pytest.mark.parametrize("nb,D,La,Lb", [(8, 10, 2047, 2047), (2, 3, 5, 1), (1, 4, 4000, 4000),
+                                        (2, 2, 30000, 20000)])
+def test_outer_autotune_both_shapes(fcs, orc, nb, D, La, Lb):
+    """fcs_outer_autotune times both block shapes: its output (the shape
+    timed last, twice the threads where there are two) and a later
+    fcs_sketch_outer of the same shape (the tuner's choice) both equal the
+    oracle; the last case (P = 2^16) has only the two-pass route."""
+    c = fcs.Context()
+    fa = synth.gaussian(95, (nb, D, La))
+    fb = synth.gaussian(96, (nb, D, Lb))
+    nt, last = fcs.fcs_outer_autotune(c, cuda(fa), cuda(fb))
+    P = 1 << max(4, (La + Lb - 2).bit_length())
+    if P > 16384:
+        assert nt == 0
+    else:
+        base = max(32, P // 32)
+        assert nt in (base, 2 * base) if 2 * base <= 1024 else nt == base
+    got = host(fcs.fcs_sketch_outer(c, cuda(fa), cuda(fb)))
+    last = host(last)
+    for b in range(nb):
+        ref = orc.outer_combine(fa[b].astype(np.float64), fb[b].astype(np.float64))
+        assert_sketch_close(last[b], ref, what=f"last timed shape, item {b}")
+        assert_sketch_close(got[b], ref, what=f"tuned shape, item {b}")
+    c.close()
+
+
 def test_kronecker_chain_small(fcs, ctx, orc):
     """FCS(A o B) from GPU sketches of A (modes 1,2) and B (modes 3,4) equals
     the oracle's dense FCS of the materialised order-4 tensor."""
