@@ -8,7 +8,7 @@ factor-transpose launch) and computes the sketches.  Unit: sketches/s (one sketc
 Jt, so a step yields D sketches).
 
 With N = 1 the default line also carries the metric's other parts as
-sub-results under the keys `dense`, `kron` and `serve` (skip them with
+sub-results under the keys `dense`, `kron`, `batch` and `serve` (skip them with
 --no-extra); each has its own roofline, clock record, end-to-end leg and CPU
 baseline (serve: capacity, p50/p99 latency and an accuracy check of served
 results against direct calls).
@@ -1219,7 +1219,7 @@ def main():
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="default workload only: skip the dense, kron and serve sub-results")
+                    help="default workload only: skip the dense, kron, batch and serve sub-results")
     ap.add_argument("--clock-window-s", type=float, default=1.0,
                     help="seconds of untimed steps, sampled for clocks, before the timed ones")
     ap.add_argument("--cpu-budget-s", type=float, default=10.0,
@@ -1245,9 +1245,10 @@ def main():
     if res is not None and args.workload == "cp" and world == 1 and not args.no_extra:
         # the metric's other parts on one GPU: the dense route and both
         # contractions (RTPM step), Kronecker compression with recovery (HBM
-        # rooflines), and the served path against the plain one (p50/p99)
+        # rooflines), the batched launch chain against one launch per
+        # problem, and the served path against the plain one (p50/p99)
         extra = {}
-        for name in ("dense", "kron"):
+        for name in ("dense", "kron", "batch"):
             extra[name] = measure(name, args, rank, world, local_rank, args.steps, args.warmup)
         extra["serve"] = run_serve(args, rank, world, local_rank)
         res.update(extra)
